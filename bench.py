@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the many-replica Metropolis sweep (flip attempts/s).
+
+One step = one pass of the hot path over one batch: anneal every replica of
+the workload through all its sweeps (structured kernel) and decode every final
+state into a path.  The QUBO and the threshold tables are built before the
+timed region (inputs resident in HBM); the end-to-end figure (`e2e`) rebuilds
+the QUBO from the host field and reads every result back to pinned host memory
+inside the timed region, through the same C ABI a user calls.
+
+Workload (default): 10x10 field, 10% obstacles dropped by a seeded Bernoulli
+draw (90 cells, n = 8100 variables), int32 dE / int64 energies, 1024 replicas
+x 5000 sweeps, geometric T 1e3 -> 1, seed 1.  flip attempts = R * S * (C-1)^2.
+
+`--impl reference` times the CPU oracle (plain C, one thread per replica) on a
+bounded sample of the same workload.
+
+Multi-GPU: replicas shard with no collective on the data path (weak scaling:
+every rank anneals its own 1024 replicas, streams offset by rank); the barrier
+and the max-over-ranks time reduction are the only communication.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "flip attempts/s on 1 GB300; time-to-within-1%-of-best path, learned vs plain"
+UNIT = "flip attempts/s"
+# algorithmic integer operations per flip attempt of the structured sweep: the
+# neighbour field of a one-hot state (2 adds), r' and c' (2), 2r'-1 and 2c'-1 (4),
+# the A, A, B products (3), two sums (2), the sign (2), the two comparisons (2)
+OPS_PER_ATTEMPT = 17
+SMS, INT_LANES_PER_SM = 152, 128
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="10x10-p0.10")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-dense", action="store_true")
+    ap.add_argument("--replicas-per-cta", type=int, default=0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ["qp_kernels.cu", "qp_internal.h"]:
+        h.update(open(os.path.join(ROOT, "paper_2608_25376_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_tag):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "sweep_structured_10x10.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
+    t = re.search(rf"{kernel_tag}_dram_bytes_per_launch_full:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(w, P, max_seconds=20.0):
+    """The oracle as it stands on this host's cores, on a bounded sample of the
+    workload: `cores` replicas, each through a prefix of the sweeps sized to about
+    max_seconds of CPU work (all sweeps when that fits)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    S = w["n_sweeps"]
+    # size the sweep count from a short probe
+    probe_s = max(1, min(S, 50))
+    t = time.perf_counter()
+    oracle.anneal_structured(P, 1, S, seed=w["seed"], sweep_end=probe_s, n_threads=1)
+    per_sweep = (time.perf_counter() - t) / probe_s
+    sweeps = int(max(1, min(S, max_seconds / max(per_sweep, 1e-9))))
+    t = time.perf_counter()
+    oracle.anneal_structured(P, cores, S, seed=w["seed"], sweep_end=sweeps, n_threads=cores)
+    dt = time.perf_counter() - t
+    attempts = cores * sweeps * (P.C - 1) ** 2
+    return {"value": attempts / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} replicas x sweeps [0,{sweeps}) of {S}, {P.C} cells, one thread per replica",
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2608_25376_gb300 import inputs
+    w = inputs.WORKLOADS[args.workload]
+    f = w["field"]()
+    P = oracle.Problem(f.rows, f.cols, f.free_mask, f.start)
+    cores = os.cpu_count() or 1
+    S = w["n_sweeps"]
+    # bounded step: `cores` replicas through a sweep prefix worth ~ 10 s of CPU
+    t = time.perf_counter()
+    oracle.anneal_structured(P, 1, S, seed=w["seed"], sweep_end=20, n_threads=1)
+    per_sweep = (time.perf_counter() - t) / 20
+    sweeps = int(max(1, min(S, 10.0 / max(per_sweep, 1e-9))))
+    for _ in range(args.warmup):
+        oracle.anneal_structured(P, cores, S, seed=w["seed"], sweep_end=min(sweeps, 5), n_threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.anneal_structured(P, cores, S, seed=w["seed"], sweep_end=sweeps, n_threads=cores)
+        times.append(time.perf_counter() - t)
+    attempts = cores * sweeps * (P.C - 1) ** 2
+    ms = 1e3 * statistics.mean(times)
+    val = attempts / (ms / 1e3)
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{args.workload} structured", "cells": P.C, "replicas": cores,
+                       "sweeps": f"[0,{sweeps}) of {S}", "schedule": "geometric 1e3->1",
+                       "parallelism": "replicas over host threads"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{cores} replicas x sweeps [0,{sweeps}) of {S} per step"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import fcntl
+    from paper_2608_25376_gb300 import build as qbuild
+    os.makedirs(qbuild.BUILD, exist_ok=True)
+    with open(os.path.join(qbuild.BUILD, ".lock"), "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        qbuild.build()
+        fcntl.flock(lk, fcntl.LOCK_UN)
+    from paper_2608_25376_gb300 import inputs, qpath
+
+    w = inputs.WORKLOADS[args.workload]
+    f = w["field"]()
+    R, S, seed = w["replicas"], w["n_sweeps"], w["seed"]
+    dense_too = not args.no_dense
+    flags = qpath.QP_STRUCTURED | (qpath.QP_DENSE if dense_too else 0)
+    h = qpath.qp_build_qubo(f, flags=flags)
+    info = h.info
+    C, n = info["C"], info["n"]
+    attempts = R * S * (C - 1) ** 2
+    sc = qpath.schedule(S)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    states = torch.zeros((R, n), dtype=torch.uint8, device=dev)
+    E = torch.zeros(R, dtype=torch.int64, device=dev)
+    best = torch.zeros(R, dtype=torch.int64, device=dev)
+    acc = torch.zeros(R, dtype=torch.int64, device=dev)
+    paths = torch.zeros((R, C), dtype=torch.int32, device=dev)
+    lens = torch.zeros(R, dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    offset = rank * R
+    rpc = args.replicas_per_cta
+
+    def step(kernel=qpath.QP_KERNEL_STRUCTURED):
+        qpath.qp_anneal_ex(h, R, sc, seed, None, states, E, best, kernel=kernel, replicas_per_cta=rpc,
+                           replica_offset=offset, accepts_out=acc, stream=stream)
+        qpath.qp_decode_batch(h, R, states, paths, lens, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k)  # evict L2 between timed steps (outside the events)
+            ev[k][0].record(stream)
+            qpath.qp_anneal_ex(h, R, sc, seed, None, states, E, best, kernel=qpath.QP_KERNEL_STRUCTURED,
+                               replicas_per_cta=rpc, replica_offset=offset, accepts_out=acc, stream=stream)
+            ev[k][1].record(stream)
+            qpath.qp_decode_batch(h, R, states, paths, lens, stream=stream)
+            ev[k][2].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(c) for a, _, c in ev]
+    anneal_ms = [a.elapsed_time(b) for a, b, _ in ev]
+    ms = statistics.mean(step_ms)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * attempts / (ms_max / 1e3)
+    feasible = int((lens >= 0).sum().item())
+    best_len = int(lens[lens >= 0].min().item()) if feasible else None
+
+    pk, pk_kind = peaks()
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    peak_tops = SMS * INT_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    ann_ms = statistics.mean(anneal_ms)
+    achieved_tops = OPS_PER_ATTEMPT * attempts / (ann_ms / 1e3) / 1e12
+    traffic = recorded_traffic("structured")
+    roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
+                "frac": achieved_tops / peak_tops, "traffic": traffic,
+                "kernel": "k_sweep_structured", "kernel_ms": ann_ms,
+                "note": (f"int32 ops: {OPS_PER_ATTEMPT} algorithmic ops per flip attempt x attempts / kernel time; "
+                         f"peak = {SMS} SMs x {INT_LANES_PER_SM} lanes x {sm_mhz:.0f} MHz ({pk_kind} clock)")}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"{args.workload} structured", "field": f"{f.rows}x{f.cols}", "cells": C,
+                       "variables": n, "replicas": R, "sweeps": S, "schedule": "geometric 1e3->1",
+                       "seed": seed, "attempts_per_step": attempts, "l2": "flushed between steps (512 MB write)",
+                       "parallelism": f"replicas x {world} GPU(s), no collective on the data path"},
+            "roofline": roofline,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk,
+            "result": {"feasible_replicas": feasible, "best_length": best_len,
+                       "accepts_per_attempt": float(acc.sum().item()) / attempts}}
+
+    if dense_too and not args.no_dense and rank == 0:
+        dms = []
+        with torch.cuda.stream(stream):
+            step(qpath.QP_KERNEL_DENSE)
+            for k in range(2):
+                flush.fill_(k)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                qpath.qp_anneal_ex(h, R, sc, seed, None, states, E, best, kernel=qpath.QP_KERNEL_DENSE,
+                                   replica_offset=offset, accepts_out=acc, stream=stream)
+                b.record(stream)
+                b.synchronize()
+                dms.append(a.elapsed_time(b))
+        dacc = float(acc.sum().item())
+        sbytes = 2  # int16 dense S for this workload
+        col_bytes = dacc * ((n + 7) // 8 * 8) * sbytes
+        dm = statistics.mean(dms)
+        line["variants"] = {"dense": {"value": attempts / (dm / 1e3), "unit": UNIT, "kernel_ms": dm,
+                                      "column_bytes_per_launch": col_bytes,
+                                      "column_GBps": col_bytes / (dm / 1e3) / 1e9,
+                                      "hbm_peak_GBps": pk.get("hbm_gbs"), "peak_kind": pk_kind}}
+
+    if not args.no_e2e:
+        pin_states = torch.empty((R, n), dtype=torch.uint8, pin_memory=True)
+        pin_E = torch.empty(R, dtype=torch.int64, pin_memory=True)
+        pin_best = torch.empty(R, dtype=torch.int64, pin_memory=True)
+        pin_paths = torch.empty((R, C), dtype=torch.int32, pin_memory=True)
+        pin_lens = torch.empty(R, dtype=torch.int64, pin_memory=True)
+        mask = np.ascontiguousarray(f.free_mask, np.uint8)
+        e_times = []
+        n_e2e = max(1, min(args.steps, 3))
+        for k in range(n_e2e):
+            flush.fill_(k)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fld = inputs.Field(f.rows, f.cols, mask, f.start)
+            h2 = qpath.qp_build_qubo(fld, flags=qpath.QP_STRUCTURED)
+            qpath.qp_anneal_ex(h2, R, sc, seed, None, pin_states, pin_E, pin_best, replica_offset=offset,
+                               stream=stream)
+            qpath.qp_decode_batch(h2, R, pin_states, pin_paths, pin_lens, stream=stream)
+            torch.cuda.synchronize()
+            e_times.append(time.perf_counter() - t0)
+            h2.close()
+        Cp = (C + 7) // 8 * 8
+        h2d = mask.nbytes + C * Cp * 2 + C * C * 4 + R * n  # field, d (int16 + int32), states for decode
+        d2h = R * n + 16 * R + R * C * 4 + 8 * R
+        em = statistics.mean(e_times)
+        line["e2e"] = {"value": world * attempts / em, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "ms_per_step": em * 1e3,
+                       "api": "qp_build_qubo + qp_anneal_ex + qp_decode_batch on pinned host buffers"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        P = oracle.Problem(f.rows, f.cols, f.free_mask, f.start)
+        line["cpu_baseline"] = cpu_baseline(w, P)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

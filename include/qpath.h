@@ -1,0 +1,177 @@
+/*
+ * qpath.h -- C ABI of libqpath, a GB300 (sm_103a) many-replica Metropolis
+ * annealer for the one-hot UAV path QUBO of "GPU-Accelerated Quantum
+ * Annealing-Inspired UAV Path Planning for Smart Agriculture".
+ *
+ * The paper's pipeline (Algorithm 1) is: travel-cost matrix from the grid
+ * (Section II) -> one-hot variables x_{t,i} -> H_visit + H_time (Eqs. 4, 5) ->
+ * H_dist (Eq. 3) -> H_QUBO (Eq. 6) -> a GPU sampler -> the path read off the
+ * best state.  This library is that pipeline with its own sampler:
+ *   qp_build_qubo / qp_build_from_dense   the QUBO (Section II, Eqs. 3-6)
+ *   qp_anneal / qp_anneal_ex / _batch     many independent Metropolis chains
+ *                                         (the role of the paper's parallel
+ *                                         annealing engine, Section IV-A)
+ *   qp_decode_path / qp_decode_batch      the path reconstruction step of
+ *                                         Algorithm 1
+ *
+ * Conventions shared by every call
+ *   Variables.  k = t*C + i, t = step, i = cell id; C free cells numbered in
+ *     row-major grid order; n = C*C.  The start cell s is clamped: x_{0,s} = 1,
+ *     the rest of row 0 and of column s are 0 and never proposed.
+ *   Energy.  E(x) = B*sum_{t<C-1} sum_{i,j} d_ij x_{t,i} x_{t+1,j}
+ *                 + A*sum_i (1 - sum_t x_{t,i})^2 + A*sum_t (1 - sum_i x_{t,i})^2
+ *     (Eqs. 3-6 with every penalty range over 0..C-1), an exact int64.  A
+ *     multiplies the penalties (the paper's lambda_p), B the distance term.
+ *   Distances.  d_ij = round(scale * sqrt(dr^2 + dc^2)) in exact integers.
+ *   Random numbers.  Philox4x32-10, key (seed_lo, seed_hi), counter
+ *     (k>>2, sweep, replica, 0x51505448); the draw of k is output word k&3.
+ *   Schedule.  T_s = T0*(T1/T0)^(s/(n_sweeps-1)) (T0 if n_sweeps == 1).
+ *     Proposal k in sweep s is accepted iff dE <= 0, or dE < len_s and
+ *     u < floor(2^32 exp(-dE/T_s)); len_s is the first dE whose threshold is 0.
+ *     Tables are built on the host in double precision.
+ *   Sweeps.  Sweep s proposes every free k once, in increasing k.
+ *   Best energy.  Minimum of E over the ends of the sweeps run at which every
+ *     row and column sum is 1 (no test for a QUBO without path structure);
+ *     INT64_MAX if there was none.
+ *   Pointers.  Every buffer is owned by the caller and may be host or device
+ *     memory (told apart with cudaPointerGetAttributes).  When every output of
+ *     a call is device memory the call is asynchronous on `cuda_stream`
+ *     (a cudaStream_t, NULL = legacy default stream); otherwise it returns
+ *     after the results are in the caller's buffers.
+ *   Errors.  Every call returns a status and never aborts; qp_last_error()
+ *     gives a message for the calling thread.  Handles are not thread-safe:
+ *     use one handle per host thread, or serialise calls on it.
+ */
+#ifndef QPATH_H
+#define QPATH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QP_OK = 0,
+  QP_EINVAL = 1,       /* bad argument                                     */
+  QP_ENOMEM = 2,       /* host or device allocation failed                 */
+  QP_ERANGE = 3,       /* a value does not fit the integer types used      */
+  QP_ECUDA = 4,        /* a CUDA call failed                               */
+  QP_ETIMEOUT = 5,     /* a bounded device wait gave up                    */
+  QP_EINFEASIBLE = 6   /* decode: the state is not a one-hot permutation   */
+} qp_status;
+
+typedef struct qp_handle qp_handle;
+
+/* A grid field (Section II).  free_mask[r*cols + c] = 1 marks a cell to
+ * visit; NULL means every cell.  start is the grid index of the start cell and
+ * must be free. */
+typedef struct {
+  int32_t rows, cols;
+  const uint8_t *free_mask;
+  int32_t start;
+} qp_field;
+
+/* Geometric schedule over n_sweeps sweeps; a call runs sweeps
+ * [sweep_begin, sweep_end), which makes a run resumable: running [0, S) equals
+ * running [0, m) and then [m, S) from the states it returned. */
+typedef struct {
+  int32_t n_sweeps;
+  double T0, T1;
+  int32_t sweep_begin, sweep_end;
+} qp_schedule;
+
+/* qp_build_qubo flags */
+enum { QP_DENSE = 1, QP_STRUCTURED = 2, QP_DIST_I16 = 4 };
+/* qp_anneal_opts.kernel */
+enum { QP_KERNEL_AUTO = 0, QP_KERNEL_DENSE = 1, QP_KERNEL_STRUCTURED = 2 };
+
+typedef struct {
+  int32_t kernel;            /* QP_KERNEL_*; AUTO = structured when built     */
+  int32_t replicas_per_cta;  /* warps (= replicas) per CTA; 0 = tuned default */
+  int32_t replica_offset;    /* global index of replica 0 (its RNG stream)    */
+  int64_t *accepts_out;      /* optional [R]: accepted flips per replica      */
+} qp_anneal_opts;
+
+/* Section II and Eqs. 3-6 (Algorithm 1, first five steps): build the path
+ * QUBO of a field.  A <= 0 selects A = 2*max d (penalty above any one step).
+ * B >= 1 weights the distance term; scale > 0 (100 = centi-units).
+ * flags: QP_STRUCTURED keeps the C x C distance matrix on the device (the
+ * structured sweep's input; int16 when QP_DIST_I16 is set or every entry
+ * fits); QP_DENSE also stores the n x n matrix S of the dense form (int16 on
+ * the device when every entry fits).  flags == 0 means QP_STRUCTURED.
+ * Errors: QP_EINVAL (bad field, start not free, fewer than 2 cells),
+ * QP_ERANGE (|dE| bound or d beyond int32), QP_ENOMEM, QP_ECUDA.
+ * *out receives a handle owned by the caller (free with qp_destroy). */
+qp_status qp_build_qubo(const qp_field *field, int32_t A, int32_t B, int32_t scale,
+                        int32_t flags, qp_handle **out);
+
+/* A generic QUBO in dense form: E(x) = sum_k S_kk x_k + sum_{k<l} S_kl x_k x_l
+ * + c0 with S symmetric (n x n int32, row-major, host memory).  frozen (n
+ * bytes, NULL = none) marks variables that are never proposed; they take
+ * frozen_val (NULL = 0).  The dense form of Eq. 6 is one such QUBO.
+ * Errors: QP_EINVAL (n < 1, S not symmetric), QP_ERANGE (a row's absolute sum
+ * beyond int32), QP_ENOMEM, QP_ECUDA. */
+qp_status qp_build_from_dense(const int32_t *S, int64_t n, const uint8_t *frozen,
+                              const uint8_t *frozen_val, int64_t c0, qp_handle **out);
+
+/* Sizes of a handle: n variables, C cells (0 for a generic QUBO), c0, max d
+ * (0 for a generic QUBO), and the penalty weight A actually used. Any output
+ * pointer may be NULL. */
+qp_status qp_qubo_info(const qp_handle *h, int64_t *n_vars, int32_t *n_cells, int64_t *c0,
+                       int32_t *max_d, int32_t *A_used);
+
+/* The dense form S (n x n int32, caller-owned host buffer) of the handle. */
+qp_status qp_export_dense(const qp_handle *h, int32_t *S_out);
+
+/* The distance matrix d (C x C int32, caller-owned host buffer). QP_EINVAL
+ * for a generic QUBO. */
+qp_status qp_export_dist(const qp_handle *h, int32_t *d_out);
+
+/* The acceptance thresholds of sweep `sweep` of `sched`: out[0] = 0xFFFFFFFF,
+ * out[dE] = floor(2^32 exp(-dE/T_s)) for 1 <= dE < len.  *len_out = len.
+ * QP_ERANGE if cap < len (len is still written). out may be NULL. */
+qp_status qp_thresholds(const qp_schedule *sched, int32_t sweep, uint32_t *out, int32_t cap,
+                        int32_t *len_out);
+
+/* Anneal `replicas` independent chains of the handle's QUBO over the sweeps
+ * [sweep_begin, sweep_end) of `sched` (the sampler step of Algorithm 1).
+ * init_states: R*n bytes (0/1, t-major) or NULL for the all-zero start; the
+ *   clamp / frozen values are applied on top.
+ * states_out: R*n bytes, the final states.  energies_out: R int64 final E.
+ * best_out: R int64 best feasible E (NULL allowed).
+ * Same as qp_anneal_ex with every option at its default. */
+qp_status qp_anneal(qp_handle *h, int32_t replicas, const qp_schedule *sched, uint64_t seed,
+                    const uint8_t *init_states, uint8_t *states_out, int64_t *energies_out,
+                    int64_t *best_out, void *cuda_stream);
+
+/* qp_anneal with options (opts may be NULL).  The kernel choice changes the
+ * speed, never the result: both kernels follow the same sequential sweep. */
+qp_status qp_anneal_ex(qp_handle *h, int32_t replicas, const qp_schedule *sched,
+                       uint64_t seed, const uint8_t *init_states, uint8_t *states_out,
+                       int64_t *energies_out, int64_t *best_out, const qp_anneal_opts *opts,
+                       void *cuda_stream);
+
+/* Algorithm 1 last step: the flight path of one state (n bytes, host or
+ * device).  path_out[t] = cell id flown at step t (C int32, host), *length_out
+ * = sum_t d(path[t], path[t+1]) (host).  QP_EINFEASIBLE if a row or column
+ * sum is not 1 (outputs untouched). */
+qp_status qp_decode_path(const qp_handle *h, const uint8_t *state, int32_t *path_out,
+                         int64_t *length_out);
+
+/* Decode R states on the device: paths_out [R*C] int32, lengths_out [R] int64
+ * (-1 where the state is infeasible).  Pointers host or device. */
+qp_status qp_decode_batch(const qp_handle *h, int32_t replicas, const uint8_t *states,
+                          int32_t *paths_out, int64_t *lengths_out, void *cuda_stream);
+
+/* Free a handle and its device memory (NULL is ignored). */
+void qp_destroy(qp_handle *h);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *qp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QPATH_H */

@@ -1,0 +1,591 @@
+// Host side of libqpath: argument checks, the QUBO build of Section II and
+// Eqs. 3-6, the schedule and acceptance-threshold tables, buffer staging and
+// kernel dispatch, and path decoding (Algorithm 1, last step).  The public
+// contract of every function is documented in include/qpath.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "qp_internal.h"
+
+using namespace qp;
+
+// --------------------------------------------------------------------------- errors
+namespace {
+thread_local std::string g_err;
+
+qp_status fail(qp_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define QP_CU(call)                                                                    \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(e_ == cudaErrorMemoryAllocation ? QP_ENOMEM : QP_ECUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                  \
+  } while (0)
+
+#define QP_TRY(expr)              \
+  do {                            \
+    qp_status s_ = (expr);        \
+    if (s_ != QP_OK) return s_;   \
+  } while (0)
+
+int round_up_i(int x, int m) { return (x + m - 1) / m * m; }
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// A device allocation owned by a handle, grown on demand.
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  qp_status ensure(size_t want) {
+    if (want <= bytes) return QP_OK;
+    release();
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return fail(QP_ENOMEM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+    }
+    bytes = want;
+    return QP_OK;
+  }
+  template <typename T>
+  T *as() const { return static_cast<T *>(p); }
+};
+
+// Exact round(scale * sqrt(q)): r = floor(sqrt(N)) for N = scale^2 q by a
+// floating-point estimate corrected in integers, then round half up, which
+// is round(sqrt(N)) because N - r^2 > r  <=>  sqrt(N) > r + 1/2.
+int64_t round_scaled_sqrt(int64_t q, int64_t scale) {
+  const int64_t N = scale * scale * q;
+  int64_t r = (int64_t)std::sqrt((double)N);
+  while (r > 0 && r * r > N) --r;
+  while ((r + 1) * (r + 1) <= N) ++r;
+  return (N - r * r > r) ? r + 1 : r;
+}
+
+// --------------------------------------------------------------------------- schedules
+double temperature(const qp_schedule &sc, int s) {
+  if (sc.n_sweeps <= 1) return sc.T0;
+  return sc.T0 * std::pow(sc.T1 / sc.T0, (double)s / (double)(sc.n_sweeps - 1));
+}
+
+// thr[dE] = floor(2^32 exp(-dE/T)) for dE >= 1 until it reaches 0; thr[0] unused.
+void build_thresholds(double T, std::vector<uint32_t> &out) {
+  out.clear();
+  out.push_back(0xFFFFFFFFu);
+  for (int64_t de = 1;; ++de) {
+    const double v = std::floor(std::ldexp(std::exp(-(double)de / T), 32));
+    if (v <= 0.0) break;
+    out.push_back((uint32_t)v);
+  }
+}
+
+qp_status check_schedule(const qp_schedule *sc) {
+  if (!sc) return fail(QP_EINVAL, "schedule is NULL");
+  if (sc->n_sweeps < 1) return fail(QP_EINVAL, "n_sweeps must be >= 1");
+  if (!(sc->T0 > 0.0) || !(sc->T1 > 0.0) || !std::isfinite(sc->T0) || !std::isfinite(sc->T1))
+    return fail(QP_EINVAL, "temperatures must be finite and > 0");
+  if (sc->T0 > 1e8 || sc->T1 > 1e8) return fail(QP_ERANGE, "temperatures above 1e8 make tables too large");
+  if (sc->sweep_begin < 0 || sc->sweep_end < sc->sweep_begin || sc->sweep_end > sc->n_sweeps)
+    return fail(QP_EINVAL, "need 0 <= sweep_begin <= sweep_end <= n_sweeps");
+  return QP_OK;
+}
+
+struct SchedKey {
+  int dev;
+  int32_t n;
+  uint64_t t0, t1;
+  bool operator<(const SchedKey &o) const {
+    return std::tie(dev, n, t0, t1) < std::tie(o.dev, o.n, o.t0, o.t1);
+  }
+};
+
+struct SchedEntry {
+  DevBuf thr, off, len;
+  DeviceSchedule view;
+};
+
+std::mutex g_sched_mu;
+std::map<SchedKey, std::unique_ptr<SchedEntry>> g_sched;
+
+// Device tables of a schedule (all n_sweeps sweeps), built once per device and
+// kept until the process exits.
+qp_status device_schedule(const qp_schedule &sc, DeviceSchedule *out) {
+  int dev = 0;
+  QP_CU(cudaGetDevice(&dev));
+  SchedKey key{dev, sc.n_sweeps, 0, 0};
+  std::memcpy(&key.t0, &sc.T0, 8);
+  std::memcpy(&key.t1, &sc.T1, 8);
+  std::lock_guard<std::mutex> lk(g_sched_mu);
+  auto it = g_sched.find(key);
+  if (it != g_sched.end()) {
+    *out = it->second->view;
+    return QP_OK;
+  }
+  auto e = std::make_unique<SchedEntry>();
+  std::vector<int64_t> off(sc.n_sweeps);
+  std::vector<int32_t> len(sc.n_sweeps);
+  std::vector<uint32_t> all, tab;
+  int32_t max_len = 0;
+  for (int s = 0; s < sc.n_sweeps; ++s) {
+    build_thresholds(temperature(sc, s), tab);
+    off[s] = (int64_t)all.size();
+    len[s] = (int32_t)tab.size();
+    max_len = std::max(max_len, len[s]);
+    all.insert(all.end(), tab.begin(), tab.end());
+  }
+  QP_TRY(e->thr.ensure(all.size() * 4));
+  QP_TRY(e->off.ensure(off.size() * 8));
+  QP_TRY(e->len.ensure(len.size() * 4));
+  QP_CU(cudaMemcpy(e->thr.p, all.data(), all.size() * 4, cudaMemcpyHostToDevice));
+  QP_CU(cudaMemcpy(e->off.p, off.data(), off.size() * 8, cudaMemcpyHostToDevice));
+  QP_CU(cudaMemcpy(e->len.p, len.data(), len.size() * 4, cudaMemcpyHostToDevice));
+  e->view.thr = e->thr.as<uint32_t>();
+  e->view.off = e->off.as<int64_t>();
+  e->view.len = e->len.as<int32_t>();
+  e->view.n_sweeps = sc.n_sweeps;
+  e->view.max_len = max_len;
+  e->view.total = (int64_t)all.size();
+  *out = e->view;
+  g_sched.emplace(key, std::move(e));
+  return QP_OK;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------- the handle
+struct qp_handle {
+  int dev = 0;
+  bool path = false;       // built from a field (structured terms available)
+  int32_t C = 0, start = 0, A = 0, B = 0, max_d = 0;
+  int64_t n = 0, c0 = 0;
+  std::vector<int32_t> d;  // C x C (host)
+  // device data
+  DevBuf d_dev;            // C x Cp, int16 or int32
+  bool d_i16 = false;
+  int32_t Cp = 0;
+  DevBuf d32_dev;          // C x C int32 (decode, dense build)
+  DevBuf S_dev;            // n x np, int16 or int32
+  bool has_dense = false, S_i16 = false;
+  int32_t np = 0;
+  DevBuf frozen_bits, fval_bits;
+  std::vector<uint8_t> frozen_host, fval_host;  // generic QUBOs
+  // scratch
+  DevBuf gstate, hbuf, in_stage, st_stage, e_stage, b_stage, a_stage, p_stage, l_stage;
+};
+
+namespace {
+
+qp_status upload_bits(qp_handle *h, const std::vector<uint8_t> &fr, const std::vector<uint8_t> &fv) {
+  const int64_t nw = (h->n + 31) / 32;
+  std::vector<uint32_t> fb(nw, 0), vb(nw, 0);
+  for (int64_t k = 0; k < h->n; ++k) {
+    if (fr[k]) fb[k >> 5] |= 1u << (k & 31);
+    if (fr[k] && fv[k]) vb[k >> 5] |= 1u << (k & 31);
+  }
+  QP_TRY(h->frozen_bits.ensure(nw * 4));
+  QP_TRY(h->fval_bits.ensure(nw * 4));
+  QP_CU(cudaMemcpy(h->frozen_bits.p, fb.data(), nw * 4, cudaMemcpyHostToDevice));
+  QP_CU(cudaMemcpy(h->fval_bits.p, vb.data(), nw * 4, cudaMemcpyHostToDevice));
+  return QP_OK;
+}
+
+struct DevSet {
+  int prev = -1;
+  explicit DevSet(int dev) {
+    int cur = 0;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != dev) {
+      prev = cur;
+      cudaSetDevice(dev);
+    }
+  }
+  ~DevSet() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+// --------------------------------------------------------------------------- build
+extern "C" qp_status qp_build_qubo(const qp_field *f, int32_t A, int32_t B, int32_t scale,
+                                   int32_t flags, qp_handle **out) {
+  g_err.clear();
+  if (!f || !out) return fail(QP_EINVAL, "field and out must not be NULL");
+  *out = nullptr;
+  if (f->rows < 1 || f->cols < 1 || (int64_t)f->rows * f->cols > (1 << 24))
+    return fail(QP_EINVAL, "bad grid size %d x %d", f->rows, f->cols);
+  if (B < 0 || scale < 1) return fail(QP_EINVAL, "need B >= 0 and scale >= 1");
+  if (f->start < 0 || f->start >= f->rows * f->cols) return fail(QP_EINVAL, "start out of the grid");
+  if (f->free_mask && !f->free_mask[f->start]) return fail(QP_EINVAL, "start cell is an obstacle");
+  if (flags == 0) flags = QP_STRUCTURED;
+  if (flags & ~(QP_DENSE | QP_STRUCTURED | QP_DIST_I16)) return fail(QP_EINVAL, "unknown flags 0x%x", flags);
+
+  auto h = std::make_unique<qp_handle>();
+  QP_CU(cudaGetDevice(&h->dev));
+  std::vector<int32_t> cr, cc;
+  for (int r = 0; r < f->rows; ++r)
+    for (int c = 0; c < f->cols; ++c) {
+      const int g = r * f->cols + c;
+      if (f->free_mask && !f->free_mask[g]) continue;
+      if (g == f->start) h->start = (int32_t)cr.size();
+      cr.push_back(r);
+      cc.push_back(c);
+    }
+  const int C = (int)cr.size();
+  if (C < 2) return fail(QP_EINVAL, "a field needs at least 2 free cells (has %d)", C);
+  if (C > kMaxCells) return fail(QP_ERANGE, "%d cells exceed the limit %d", C, kMaxCells);
+  h->path = true;
+  h->C = C;
+  h->n = (int64_t)C * C;
+  h->d.resize((size_t)C * C);
+  int64_t maxd = 0;
+  for (int i = 0; i < C; ++i)
+    for (int j = 0; j < C; ++j) {
+      const int64_t dr = cr[i] - cr[j], dc = cc[i] - cc[j];
+      const int64_t v = round_scaled_sqrt(dr * dr + dc * dc, scale);
+      if (v > INT32_MAX) return fail(QP_ERANGE, "distance beyond int32");
+      h->d[(size_t)i * C + j] = (int32_t)v;
+      maxd = std::max(maxd, v);
+    }
+  h->max_d = (int32_t)maxd;
+  const int64_t Aeff = A > 0 ? A : 2 * maxd;
+  if (Aeff > INT32_MAX / 4) return fail(QP_ERANGE, "penalty A beyond int32/4");
+  h->A = (int32_t)Aeff;
+  h->B = B;
+  h->c0 = 2 * (int64_t)h->A * C;
+  // |dE| <= B * max_d * 2C + 2A(2C + 1) must fit int32
+  const double bound = (double)B * maxd * 2.0 * C + 2.0 * h->A * (2.0 * C + 1.0);
+  if (bound >= 2147483647.0) return fail(QP_ERANGE, "|dE| bound %.3g exceeds int32", bound);
+
+  h->Cp = round_up_i(C, 8);
+  h->d_i16 = (flags & QP_DIST_I16) || maxd <= 32767;
+  if (h->d_i16 && maxd > 32767) return fail(QP_ERANGE, "QP_DIST_I16 but max d = %lld", (long long)maxd);
+  // device copies of d
+  QP_TRY(h->d32_dev.ensure((size_t)C * C * 4));
+  QP_CU(cudaMemcpy(h->d32_dev.p, h->d.data(), (size_t)C * C * 4, cudaMemcpyHostToDevice));
+  {
+    const size_t es = h->d_i16 ? 2 : 4;
+    std::vector<uint8_t> pad((size_t)C * h->Cp * es, 0);
+    for (int i = 0; i < C; ++i)
+      for (int j = 0; j < C; ++j) {
+        const int32_t v = h->d[(size_t)i * C + j];
+        if (h->d_i16) reinterpret_cast<int16_t *>(pad.data())[(size_t)i * h->Cp + j] = (int16_t)v;
+        else reinterpret_cast<int32_t *>(pad.data())[(size_t)i * h->Cp + j] = v;
+      }
+    QP_TRY(h->d_dev.ensure(pad.size()));
+    QP_CU(cudaMemcpy(h->d_dev.p, pad.data(), pad.size(), cudaMemcpyHostToDevice));
+  }
+  if (flags & QP_DENSE) {
+    if (h->n > 65536) return fail(QP_ERANGE, "dense form of %lld variables is too large", (long long)h->n);
+    const int64_t maxS = std::max<int64_t>(2 * (int64_t)h->A, (int64_t)B * maxd);
+    h->S_i16 = maxS <= 32767;
+    h->np = round_up_i((int)h->n, 8);
+    QP_TRY(h->S_dev.ensure((size_t)h->n * h->np * (h->S_i16 ? 2 : 4)));
+    QP_CU(launch_build_dense(h->S_dev.p, h->S_i16, h->np, C, h->d32_dev.as<int32_t>(), h->A, B, 0));
+    QP_CU(cudaDeviceSynchronize());
+    std::vector<uint8_t> fr(h->n, 0), fv(h->n, 0);
+    for (int t = 0; t < C; ++t)
+      for (int i = 0; i < C; ++i)
+        if (t == 0 || i == h->start) {
+          fr[(size_t)t * C + i] = 1;
+          fv[(size_t)t * C + i] = (t == 0 && i == h->start);
+        }
+    QP_TRY(upload_bits(h.get(), fr, fv));
+    h->has_dense = true;
+  }
+  *out = h.release();
+  return QP_OK;
+}
+
+extern "C" qp_status qp_build_from_dense(const int32_t *S, int64_t n, const uint8_t *frozen,
+                                         const uint8_t *frozen_val, int64_t c0, qp_handle **out) {
+  g_err.clear();
+  if (!S || !out) return fail(QP_EINVAL, "S and out must not be NULL");
+  *out = nullptr;
+  if (n < 1 || n > 65536) return fail(QP_EINVAL, "need 1 <= n <= 65536 (got %lld)", (long long)n);
+  if (is_device_ptr(S)) return fail(QP_EINVAL, "S must be host memory");
+  auto h = std::make_unique<qp_handle>();
+  QP_CU(cudaGetDevice(&h->dev));
+  h->n = n;
+  h->c0 = c0;
+  int64_t maxabs = 0;
+  for (int64_t k = 0; k < n; ++k) {
+    int64_t rowabs = 0;
+    for (int64_t l = 0; l < n; ++l) {
+      const int32_t v = S[k * n + l];
+      if (v != S[l * n + k]) return fail(QP_EINVAL, "S is not symmetric at (%lld, %lld)", (long long)k, (long long)l);
+      rowabs += std::llabs((long long)v);
+      maxabs = std::max<int64_t>(maxabs, std::llabs((long long)v));
+    }
+    if (rowabs > INT32_MAX) return fail(QP_ERANGE, "row %lld of S has absolute sum beyond int32", (long long)k);
+  }
+  h->S_i16 = maxabs <= 32767;
+  h->np = round_up_i((int)n, 8);
+  const size_t es = h->S_i16 ? 2 : 4;
+  std::vector<uint8_t> pad((size_t)n * h->np * es, 0);
+  for (int64_t k = 0; k < n; ++k)
+    for (int64_t l = 0; l < n; ++l) {
+      if (h->S_i16) reinterpret_cast<int16_t *>(pad.data())[k * h->np + l] = (int16_t)S[k * n + l];
+      else reinterpret_cast<int32_t *>(pad.data())[k * h->np + l] = S[k * n + l];
+    }
+  QP_TRY(h->S_dev.ensure(pad.size()));
+  QP_CU(cudaMemcpy(h->S_dev.p, pad.data(), pad.size(), cudaMemcpyHostToDevice));
+  h->frozen_host.assign(n, 0);
+  h->fval_host.assign(n, 0);
+  for (int64_t k = 0; k < n; ++k) {
+    h->frozen_host[k] = frozen ? (frozen[k] != 0) : 0;
+    h->fval_host[k] = (frozen && frozen[k] && frozen_val) ? (frozen_val[k] != 0) : 0;
+  }
+  QP_TRY(upload_bits(h.get(), h->frozen_host, h->fval_host));
+  h->has_dense = true;
+  *out = h.release();
+  return QP_OK;
+}
+
+extern "C" qp_status qp_qubo_info(const qp_handle *h, int64_t *n_vars, int32_t *n_cells,
+                                  int64_t *c0, int32_t *max_d, int32_t *A_used) {
+  if (!h) return fail(QP_EINVAL, "handle is NULL");
+  if (n_vars) *n_vars = h->n;
+  if (n_cells) *n_cells = h->path ? h->C : 0;
+  if (c0) *c0 = h->c0;
+  if (max_d) *max_d = h->max_d;
+  if (A_used) *A_used = h->A;
+  return QP_OK;
+}
+
+extern "C" qp_status qp_export_dist(const qp_handle *h, int32_t *d_out) {
+  if (!h || !d_out) return fail(QP_EINVAL, "handle and d_out must not be NULL");
+  if (!h->path) return fail(QP_EINVAL, "a generic QUBO has no distance matrix");
+  std::memcpy(d_out, h->d.data(), h->d.size() * 4);
+  return QP_OK;
+}
+
+extern "C" qp_status qp_export_dense(const qp_handle *h, int32_t *S_out) {
+  if (!h || !S_out) return fail(QP_EINVAL, "handle and S_out must not be NULL");
+  if (!h->has_dense) return fail(QP_EINVAL, "handle was built without QP_DENSE");
+  DevSet ds(h->dev);
+  const size_t es = h->S_i16 ? 2 : 4;
+  std::vector<uint8_t> tmp((size_t)h->n * h->np * es);
+  QP_CU(cudaMemcpy(tmp.data(), h->S_dev.p, tmp.size(), cudaMemcpyDeviceToHost));
+  for (int64_t k = 0; k < h->n; ++k)
+    for (int64_t l = 0; l < h->n; ++l)
+      S_out[k * h->n + l] = h->S_i16 ? reinterpret_cast<int16_t *>(tmp.data())[k * h->np + l]
+                                     : reinterpret_cast<int32_t *>(tmp.data())[k * h->np + l];
+  return QP_OK;
+}
+
+extern "C" qp_status qp_thresholds(const qp_schedule *sc, int32_t sweep, uint32_t *out, int32_t cap,
+                                   int32_t *len_out) {
+  g_err.clear();
+  if (!sc) return fail(QP_EINVAL, "schedule is NULL");
+  if (sc->n_sweeps < 1 || sweep < 0 || sweep >= sc->n_sweeps) return fail(QP_EINVAL, "sweep out of range");
+  if (!(sc->T0 > 0.0) || !(sc->T1 > 0.0)) return fail(QP_EINVAL, "temperatures must be > 0");
+  std::vector<uint32_t> tab;
+  build_thresholds(temperature(*sc, sweep), tab);
+  if (len_out) *len_out = (int32_t)tab.size();
+  if (!out) return QP_OK;
+  if (cap < (int32_t)tab.size()) return fail(QP_ERANGE, "cap %d < len %zu", cap, tab.size());
+  std::memcpy(out, tab.data(), tab.size() * 4);
+  return QP_OK;
+}
+
+// --------------------------------------------------------------------------- anneal
+extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc, uint64_t seed,
+                                  const uint8_t *init, uint8_t *states_out, int64_t *energies_out,
+                                  int64_t *best_out, const qp_anneal_opts *opts, void *stream_) {
+  g_err.clear();
+  if (!h) return fail(QP_EINVAL, "handle is NULL");
+  if (R < 1) return fail(QP_EINVAL, "replicas must be >= 1");
+  if (!states_out || !energies_out) return fail(QP_EINVAL, "states_out and energies_out are required");
+  QP_TRY(check_schedule(sc));
+  qp_anneal_opts o{};
+  if (opts) o = *opts;
+  if (o.replica_offset < 0 || (int64_t)o.replica_offset + R > INT32_MAX)
+    return fail(QP_EINVAL, "replica_offset out of range");
+  int kernel = o.kernel;
+  if (kernel == QP_KERNEL_AUTO) kernel = h->path ? QP_KERNEL_STRUCTURED : QP_KERNEL_DENSE;
+  if (kernel == QP_KERNEL_STRUCTURED && !h->path) return fail(QP_EINVAL, "no structured form in this handle");
+  if (kernel == QP_KERNEL_DENSE && !h->has_dense) return fail(QP_EINVAL, "handle was built without QP_DENSE");
+  if (kernel != QP_KERNEL_STRUCTURED && kernel != QP_KERNEL_DENSE) return fail(QP_EINVAL, "unknown kernel %d", kernel);
+  if (o.replicas_per_cta < 0 || o.replicas_per_cta > kMaxWarpsPerCta)
+    return fail(QP_EINVAL, "replicas_per_cta must be in [0, %d]", kMaxWarpsPerCta);
+
+  DevSet ds(h->dev);
+  cudaStream_t st = static_cast<cudaStream_t>(stream_);
+  DeviceSchedule sched;
+  QP_TRY(device_schedule(*sc, &sched));
+  const size_t n = (size_t)h->n;
+
+  // stage host buffers
+  const uint8_t *init_d = init;
+  if (init && !is_device_ptr(init)) {
+    QP_TRY(h->in_stage.ensure((size_t)R * n));
+    QP_CU(cudaMemcpyAsync(h->in_stage.p, init, (size_t)R * n, cudaMemcpyHostToDevice, st));
+    init_d = h->in_stage.as<uint8_t>();
+  }
+  const bool st_host = !is_device_ptr(states_out);
+  const bool e_host = !is_device_ptr(energies_out);
+  const bool b_host = best_out && !is_device_ptr(best_out);
+  const bool a_host = o.accepts_out && !is_device_ptr(o.accepts_out);
+  uint8_t *st_d = states_out;
+  int64_t *e_d = energies_out, *b_d = best_out, *a_d = o.accepts_out;
+  if (st_host) { QP_TRY(h->st_stage.ensure((size_t)R * n)); st_d = h->st_stage.as<uint8_t>(); }
+  if (e_host) { QP_TRY(h->e_stage.ensure((size_t)R * 8)); e_d = h->e_stage.as<int64_t>(); }
+  if (b_host) { QP_TRY(h->b_stage.ensure((size_t)R * 8)); b_d = h->b_stage.as<int64_t>(); }
+  if (a_host) { QP_TRY(h->a_stage.ensure((size_t)R * 8)); a_d = h->a_stage.as<int64_t>(); }
+  const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+
+  LaunchInfo info;
+  if (kernel == QP_KERNEL_STRUCTURED) {
+    int W = o.replicas_per_cta ? o.replicas_per_cta : 4;
+    StructArgs a{};
+    a.C = h->C; a.Cp = h->Cp; a.start = h->start; a.A = h->A; a.B = h->B;
+    a.d = h->d_dev.p;
+    a.R = R; a.rep_offset = o.replica_offset;
+    a.sweep_begin = sc->sweep_begin; a.sweep_end = sc->sweep_end;
+    a.key0 = key0; a.key1 = key1;
+    a.thr = sched.thr; a.thr_off = sched.off; a.thr_len = sched.len;
+    a.init = init_d; a.states_out = st_d; a.E_out = e_d; a.best_out = b_d; a.acc_out = a_d;
+    a.nw_pad = (int32_t)structured_gstate_words(h->C);
+    const bool want_smem = structured_state_fits_smem(h->C, h->d_i16, W) &&
+                           4 * structured_gstate_words(h->C) <= 8 * 1024;
+    if (!want_smem) {
+      QP_TRY(h->gstate.ensure((size_t)R * a.nw_pad * 4));
+      a.gstate = h->gstate.as<uint32_t>();
+    }
+    QP_CU(launch_structured(a, h->d_i16, W, want_smem, st, &info));
+  } else {
+    int W = o.replicas_per_cta ? o.replicas_per_cta : 4;
+    while (W > 1 && !dense_h_fits_smem(h->n, h->path ? h->C : 0, W)) --W;
+    DenseArgs a{};
+    a.n = h->n; a.np = h->np; a.S = h->S_dev.p; a.c0 = h->c0; a.C = h->path ? h->C : 0;
+    a.frozen_bits = h->frozen_bits.as<uint32_t>(); a.fval_bits = h->fval_bits.as<uint32_t>();
+    a.R = R; a.rep_offset = o.replica_offset;
+    a.sweep_begin = sc->sweep_begin; a.sweep_end = sc->sweep_end;
+    a.key0 = key0; a.key1 = key1;
+    a.thr = sched.thr; a.thr_off = sched.off; a.thr_len = sched.len;
+    a.init = init_d; a.states_out = st_d; a.E_out = e_d; a.best_out = b_d; a.acc_out = a_d;
+    if (!dense_h_fits_smem(h->n, a.C, W)) {
+      QP_TRY(h->hbuf.ensure((size_t)R * h->np * 4));
+      a.hbuf = h->hbuf.as<int32_t>();
+    }
+    QP_CU(launch_dense(a, h->S_i16, W, st, &info));
+  }
+  if (st_host) QP_CU(cudaMemcpyAsync(states_out, st_d, (size_t)R * n, cudaMemcpyDeviceToHost, st));
+  if (e_host) QP_CU(cudaMemcpyAsync(energies_out, e_d, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
+  if (b_host) QP_CU(cudaMemcpyAsync(best_out, b_d, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
+  if (a_host) QP_CU(cudaMemcpyAsync(o.accepts_out, a_d, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
+  if (st_host || e_host || b_host || a_host || (init && init_d != init)) QP_CU(cudaStreamSynchronize(st));
+  return QP_OK;
+}
+
+extern "C" qp_status qp_anneal(qp_handle *h, int32_t R, const qp_schedule *sc, uint64_t seed,
+                               const uint8_t *init, uint8_t *states_out, int64_t *energies_out,
+                               int64_t *best_out, void *stream) {
+  return qp_anneal_ex(h, R, sc, seed, init, states_out, energies_out, best_out, nullptr, stream);
+}
+
+// --------------------------------------------------------------------------- decode
+extern "C" qp_status qp_decode_path(const qp_handle *h, const uint8_t *state, int32_t *path_out,
+                                    int64_t *length_out) {
+  g_err.clear();
+  if (!h || !state || !path_out || !length_out) return fail(QP_EINVAL, "NULL argument");
+  if (!h->path) return fail(QP_EINVAL, "a generic QUBO has no path");
+  const int C = h->C;
+  std::vector<uint8_t> x;
+  const uint8_t *xs = state;
+  if (is_device_ptr(state)) {
+    DevSet ds(h->dev);
+    x.resize((size_t)C * C);
+    QP_CU(cudaMemcpy(x.data(), state, x.size(), cudaMemcpyDeviceToHost));
+    xs = x.data();
+  }
+  std::vector<int32_t> path(C, -1), colcnt(C, 0);
+  for (int t = 0; t < C; ++t) {
+    int cnt = 0;
+    for (int i = 0; i < C; ++i)
+      if (xs[(size_t)t * C + i]) {
+        ++cnt;
+        path[t] = i;
+        ++colcnt[i];
+      }
+    if (cnt != 1) return fail(QP_EINFEASIBLE, "step %d has %d cells", t, cnt);
+  }
+  for (int i = 0; i < C; ++i)
+    if (colcnt[i] != 1) return fail(QP_EINFEASIBLE, "cell %d is visited %d times", i, colcnt[i]);
+  int64_t L = 0;
+  for (int t = 0; t + 1 < C; ++t) L += h->d[(size_t)path[t] * C + path[t + 1]];
+  std::memcpy(path_out, path.data(), C * 4);
+  *length_out = L;
+  return QP_OK;
+}
+
+extern "C" qp_status qp_decode_batch(const qp_handle *hc, int32_t R, const uint8_t *states,
+                                     int32_t *paths_out, int64_t *lengths_out, void *stream_) {
+  g_err.clear();
+  qp_handle *h = const_cast<qp_handle *>(hc);
+  if (!h || !states || !paths_out || !lengths_out || R < 1) return fail(QP_EINVAL, "bad argument");
+  if (!h->path) return fail(QP_EINVAL, "a generic QUBO has no path");
+  DevSet ds(h->dev);
+  cudaStream_t st = static_cast<cudaStream_t>(stream_);
+  const size_t n = (size_t)h->n;
+  const uint8_t *sd = states;
+  bool sync = false;
+  if (!is_device_ptr(states)) {
+    QP_TRY(h->in_stage.ensure((size_t)R * n));
+    QP_CU(cudaMemcpyAsync(h->in_stage.p, states, (size_t)R * n, cudaMemcpyHostToDevice, st));
+    sd = h->in_stage.as<uint8_t>();
+    sync = true;
+  }
+  int32_t *pd = paths_out;
+  int64_t *ld = lengths_out;
+  const bool ph = !is_device_ptr(paths_out), lh = !is_device_ptr(lengths_out);
+  if (ph) { QP_TRY(h->p_stage.ensure((size_t)R * h->C * 4)); pd = h->p_stage.as<int32_t>(); }
+  if (lh) { QP_TRY(h->l_stage.ensure((size_t)R * 8)); ld = h->l_stage.as<int64_t>(); }
+  QP_CU(launch_decode(sd, R, h->C, h->d32_dev.as<int32_t>(), pd, ld, st));
+  if (ph) QP_CU(cudaMemcpyAsync(paths_out, pd, (size_t)R * h->C * 4, cudaMemcpyDeviceToHost, st));
+  if (lh) QP_CU(cudaMemcpyAsync(lengths_out, ld, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
+  if (sync || ph || lh) QP_CU(cudaStreamSynchronize(st));
+  return QP_OK;
+}
+
+extern "C" void qp_destroy(qp_handle *h) {
+  if (!h) return;
+  DevSet ds(h->dev);
+  delete h;
+}
+
+extern "C" const char *qp_last_error(void) { return g_err.c_str(); }

@@ -1,0 +1,85 @@
+// Internal types shared by the host library (qp_host.cpp) and the kernels.
+// Not part of the public ABI (include/qpath.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "qpath.h"
+
+namespace qp {
+
+constexpr uint32_t kRngTag = 0x51505448u;  // counter word 3 of every sweep draw
+constexpr int kMaxCells = 4096;            // C limit (n = C^2 fits int32 comfortably)
+constexpr int kMaxWarpsPerCta = 16;
+
+// Thresholds of one schedule on one device: thr[off[s] + dE] for 0 <= dE < len[s].
+struct DeviceSchedule {
+  const uint32_t *thr = nullptr;
+  const int64_t *off = nullptr;
+  const int32_t *len = nullptr;
+  int32_t n_sweeps = 0;
+  int32_t max_len = 0;
+  int64_t total = 0;
+};
+
+// Arguments of the structured sweep (one warp = one replica).
+struct StructArgs {
+  int32_t C, Cp, start, A, B;
+  const void *d;             // C x Cp, int16 or int32
+  int32_t R, rep_offset;
+  int32_t sweep_begin, sweep_end;
+  uint32_t key0, key1;
+  const uint32_t *thr;
+  const int64_t *thr_off;
+  const int32_t *thr_len;
+  const uint8_t *init;       // R x n or null
+  uint8_t *states_out;       // R x n
+  int64_t *E_out, *best_out, *acc_out;  // best/acc may be null
+  uint32_t *gstate;          // R x nw_pad words when the state lives in global memory
+  int32_t nw_pad;
+};
+
+// Arguments of the dense sweep (one warp = one replica).
+struct DenseArgs {
+  int64_t n;
+  int32_t np;                // padded row stride of S (multiple of 8)
+  const void *S;             // n x np, int16 or int32
+  int64_t c0;
+  int32_t C;                 // path structure (0 = generic)
+  const uint32_t *frozen_bits, *fval_bits;  // nw words each
+  int32_t R, rep_offset;
+  int32_t sweep_begin, sweep_end;
+  uint32_t key0, key1;
+  const uint32_t *thr;
+  const int64_t *thr_off;
+  const int32_t *thr_len;
+  const uint8_t *init;
+  uint8_t *states_out;
+  int64_t *E_out, *best_out, *acc_out;
+  int32_t *hbuf;             // R x np int32 when h lives in global memory
+};
+
+struct LaunchInfo {
+  int warps_per_cta = 0;
+  int blocks = 0;
+  size_t smem = 0;
+  const char *variant = "";
+};
+
+// Kernel launchers (qp_kernels.cu).  Return cudaSuccess or the launch error.
+cudaError_t launch_structured(const StructArgs &a, bool d_i16, int warps_per_cta, bool want_state_smem,
+                              cudaStream_t st, LaunchInfo *info);
+size_t structured_gstate_words(int C);  // nw_pad for the global-state layout
+bool structured_state_fits_smem(int C, bool d_i16, int warps_per_cta);
+cudaError_t launch_dense(const DenseArgs &a, bool s_i16, int warps_per_cta, cudaStream_t st,
+                         LaunchInfo *info);
+bool dense_h_fits_smem(int64_t n, int C, int warps_per_cta);
+cudaError_t launch_build_dense(void *S, bool s_i16, int32_t np, int32_t C, const int32_t *d32,
+                               int32_t A, int32_t B, cudaStream_t st);
+cudaError_t launch_decode(const uint8_t *states, int32_t R, int32_t C, const int32_t *d32,
+                          int32_t *paths, int64_t *lengths, cudaStream_t st);
+
+}  // namespace qp

@@ -1,0 +1,229 @@
+"""Thin ctypes binding of libqpath (include/qpath.h), names as in the C ABI.
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  Buffers may be torch tensors (host or CUDA) or numpy arrays; they are
+passed by pointer and owned by the caller.  The library must be built
+(``paper_2608_25376_gb300.build.build()``); loading fails loudly if it is not.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+QP_OK, QP_EINVAL, QP_ENOMEM, QP_ERANGE, QP_ECUDA, QP_ETIMEOUT, QP_EINFEASIBLE = range(7)
+QP_DENSE, QP_STRUCTURED, QP_DIST_I16 = 1, 2, 4
+QP_KERNEL_AUTO, QP_KERNEL_DENSE, QP_KERNEL_STRUCTURED = 0, 1, 2
+E_NONE = np.iinfo(np.int64).max
+
+# every entry point include/qpath.h declares
+SYMBOLS = ["qp_build_qubo", "qp_build_from_dense", "qp_qubo_info", "qp_export_dense", "qp_export_dist",
+           "qp_thresholds", "qp_anneal", "qp_anneal_ex", "qp_decode_path", "qp_decode_batch",
+           "qp_destroy", "qp_last_error"]
+
+
+class QpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"qpath status {status}: {msg}")
+        self.status = status
+
+
+class qp_field(ct.Structure):
+    _fields_ = [("rows", ct.c_int32), ("cols", ct.c_int32), ("free_mask", ct.c_void_p), ("start", ct.c_int32)]
+
+
+class qp_schedule(ct.Structure):
+    _fields_ = [("n_sweeps", ct.c_int32), ("T0", ct.c_double), ("T1", ct.c_double),
+                ("sweep_begin", ct.c_int32), ("sweep_end", ct.c_int32)]
+
+
+class qp_anneal_opts(ct.Structure):
+    _fields_ = [("kernel", ct.c_int32), ("replicas_per_cta", ct.c_int32), ("replica_offset", ct.c_int32),
+                ("accepts_out", ct.c_void_p)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libqpath.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = lib_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libqpath is not built ({path} missing): run __graft_entry__.build()")
+            L = ct.CDLL(path)
+            vp, i32, i64, u64 = ct.c_void_p, ct.c_int32, ct.c_int64, ct.c_uint64
+            P = ct.POINTER
+            sig = {
+                "qp_build_qubo": [P(qp_field), i32, i32, i32, i32, P(vp)],
+                "qp_build_from_dense": [vp, i64, vp, vp, i64, P(vp)],
+                "qp_qubo_info": [vp, P(i64), P(i32), P(i64), P(i32), P(i32)],
+                "qp_export_dense": [vp, vp],
+                "qp_export_dist": [vp, vp],
+                "qp_thresholds": [P(qp_schedule), i32, vp, i32, P(i32)],
+                "qp_anneal": [vp, i32, P(qp_schedule), u64, vp, vp, vp, vp, vp],
+                "qp_anneal_ex": [vp, i32, P(qp_schedule), u64, vp, vp, vp, vp, P(qp_anneal_opts), vp],
+                "qp_decode_path": [vp, vp, vp, vp],
+                "qp_decode_batch": [vp, i32, vp, vp, vp, vp],
+            }
+            for name, args in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = ct.c_int
+            L.qp_destroy.argtypes = [vp]
+            L.qp_destroy.restype = None
+            L.qp_last_error.argtypes = []
+            L.qp_last_error.restype = ct.c_char_p
+            _lib = L
+    return _lib
+
+
+def qp_last_error() -> str:
+    return lib().qp_last_error().decode()
+
+
+def _check(status):
+    if status != QP_OK:
+        raise QpError(status, qp_last_error())
+
+
+def _ptr(x):
+    """Address of a torch tensor / numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("buffers must be contiguous")
+        return ct.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("buffers must be contiguous")
+        return ct.c_void_p(x.ctypes.data)
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ct.c_void_p(stream.cuda_stream)
+    return ct.c_void_p(int(stream))
+
+
+def schedule(n_sweeps, T0=1e3, T1=1.0, sweep_begin=0, sweep_end=None) -> qp_schedule:
+    return qp_schedule(int(n_sweeps), float(T0), float(T1), int(sweep_begin),
+                       int(n_sweeps if sweep_end is None else sweep_end))
+
+
+class Handle:
+    """Owns a qp_handle*; freed by qp_destroy on close / garbage collection."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def close(self):
+        if self.ptr:
+            lib().qp_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def info(self):
+        return qp_qubo_info(self)
+
+
+def qp_build_qubo(field, A=0, B=1, scale=100, flags=QP_STRUCTURED) -> Handle:
+    """field: an object with rows, cols, free_mask (uint8 numpy or None), start."""
+    mask = None if field.free_mask is None else np.ascontiguousarray(field.free_mask, np.uint8)
+    f = qp_field(int(field.rows), int(field.cols), None if mask is None else mask.ctypes.data, int(field.start))
+    out = ct.c_void_p()
+    _check(lib().qp_build_qubo(ct.byref(f), int(A), int(B), int(scale), int(flags), ct.byref(out)))
+    return Handle(out)
+
+
+def qp_build_from_dense(S, c0=0, frozen=None, frozen_val=None) -> Handle:
+    S = np.ascontiguousarray(S, np.int32)
+    fr = None if frozen is None else np.ascontiguousarray(frozen, np.uint8)
+    fv = None if frozen_val is None else np.ascontiguousarray(frozen_val, np.uint8)
+    out = ct.c_void_p()
+    _check(lib().qp_build_from_dense(_ptr(S), S.shape[0], _ptr(fr), _ptr(fv), int(c0), ct.byref(out)))
+    return Handle(out)
+
+
+def qp_qubo_info(h: Handle) -> dict:
+    n, C, c0, md, A = ct.c_int64(), ct.c_int32(), ct.c_int64(), ct.c_int32(), ct.c_int32()
+    _check(lib().qp_qubo_info(h.ptr, ct.byref(n), ct.byref(C), ct.byref(c0), ct.byref(md), ct.byref(A)))
+    return dict(n=n.value, C=C.value, c0=c0.value, max_d=md.value, A=A.value)
+
+
+def qp_export_dense(h: Handle) -> np.ndarray:
+    n = qp_qubo_info(h)["n"]
+    S = np.zeros((n, n), np.int32)
+    _check(lib().qp_export_dense(h.ptr, _ptr(S)))
+    return S
+
+
+def qp_export_dist(h: Handle) -> np.ndarray:
+    C = qp_qubo_info(h)["C"]
+    d = np.zeros((C, C), np.int32)
+    _check(lib().qp_export_dist(h.ptr, _ptr(d)))
+    return d
+
+
+def qp_thresholds(sched: qp_schedule, sweep: int) -> np.ndarray:
+    n = ct.c_int32()
+    _check(lib().qp_thresholds(ct.byref(sched), int(sweep), None, 0, ct.byref(n)))
+    out = np.zeros(n.value, np.uint32)
+    _check(lib().qp_thresholds(ct.byref(sched), int(sweep), _ptr(out), n.value, ct.byref(n)))
+    return out
+
+
+def qp_anneal(h: Handle, replicas, sched, seed, init_states, states_out, energies_out, best_out=None,
+              stream=None):
+    _check(lib().qp_anneal(h.ptr, int(replicas), ct.byref(sched), ct.c_uint64(seed), _ptr(init_states),
+                           _ptr(states_out), _ptr(energies_out), _ptr(best_out), _stream(stream)))
+
+
+def qp_anneal_ex(h: Handle, replicas, sched, seed, init_states, states_out, energies_out, best_out=None,
+                 kernel=QP_KERNEL_AUTO, replicas_per_cta=0, replica_offset=0, accepts_out=None, stream=None):
+    o = qp_anneal_opts(int(kernel), int(replicas_per_cta), int(replica_offset),
+                       None if accepts_out is None else _ptr(accepts_out).value)
+    _check(lib().qp_anneal_ex(h.ptr, int(replicas), ct.byref(sched), ct.c_uint64(seed), _ptr(init_states),
+                              _ptr(states_out), _ptr(energies_out), _ptr(best_out), ct.byref(o),
+                              _stream(stream)))
+
+
+def qp_decode_path(h: Handle, state):
+    """-> (path int32[C], length) or None when the state is not a path."""
+    C = qp_qubo_info(h)["C"]
+    path = np.zeros(C, np.int32)
+    L = ct.c_int64()
+    st = lib().qp_decode_path(h.ptr, _ptr(state), _ptr(path), ct.byref(L))
+    if st == QP_EINFEASIBLE:
+        return None
+    _check(st)
+    return path, L.value
+
+
+def qp_decode_batch(h: Handle, replicas, states, paths_out, lengths_out, stream=None):
+    _check(lib().qp_decode_batch(h.ptr, int(replicas), _ptr(states), _ptr(paths_out), _ptr(lengths_out),
+                                 _stream(stream)))
+
+
+def qp_destroy(h: Handle):
+    h.close()
