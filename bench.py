@@ -56,6 +56,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--replicas-per-cta", type=int, default=0)
+    ap.add_argument("--structured-kernel", default="rows", choices=["rows", "flat"])
+    ap.add_argument("--profile-case", default=None, choices=["rows", "flat", "dense"],
+                    help="run one warm-up and one measured launch of that kernel on a sub-range of "
+                         "the workload (--sweep-window, --replicas), for ncu captures")
+    ap.add_argument("--sweep-window", nargs=2, type=int, default=[0, 100])
+    ap.add_argument("--replicas", type=int, default=0)
     return ap.parse_args()
 
 
@@ -239,8 +245,9 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     offset = rank * R
     rpc = args.replicas_per_cta
+    skernel = qpath.QP_KERNEL_STRUCTURED if args.structured_kernel == "rows" else qpath.QP_KERNEL_STRUCTURED_FLAT
 
-    def step(kernel=qpath.QP_KERNEL_STRUCTURED):
+    def step(kernel=skernel):
         qpath.qp_anneal_ex(h, R, sc, seed, None, states, E, best, kernel=kernel, replicas_per_cta=rpc,
                            replica_offset=offset, accepts_out=acc, stream=stream)
         qpath.qp_decode_batch(h, R, states, paths, lens, stream=stream)
@@ -261,7 +268,7 @@ def run_ours(args):
         for k in range(args.steps):
             flush.fill_(k)  # evict L2 between timed steps (outside the events)
             ev[k][0].record(stream)
-            qpath.qp_anneal_ex(h, R, sc, seed, None, states, E, best, kernel=qpath.QP_KERNEL_STRUCTURED,
+            qpath.qp_anneal_ex(h, R, sc, seed, None, states, E, best, kernel=skernel,
                                replicas_per_cta=rpc, replica_offset=offset, accepts_out=acc, stream=stream)
             ev[k][1].record(stream)
             qpath.qp_decode_batch(h, R, states, paths, lens, stream=stream)
@@ -289,7 +296,8 @@ def run_ours(args):
     traffic = recorded_traffic("structured")
     roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
                 "frac": achieved_tops / peak_tops, "traffic": traffic,
-                "kernel": "k_sweep_structured", "kernel_ms": ann_ms,
+                "kernel": "k_sweep_rows" if args.structured_kernel == "rows" else "k_sweep_structured",
+                "kernel_ms": ann_ms,
                 "note": (f"int32 ops: {OPS_PER_ATTEMPT} algorithmic ops per flip attempt x attempts / kernel time; "
                          f"peak = {SMS} SMs x {INT_LANES_PER_SM} lanes x {sm_mhz:.0f} MHz ({pk_kind} clock)")}
 
@@ -368,8 +376,44 @@ def run_ours(args):
     return 0
 
 
+def run_profile_case(args):
+    """One warm-up and one measured launch, nothing else on the GPU."""
+    import torch
+    from paper_2608_25376_gb300 import build as qbuild
+    qbuild.build()
+    from paper_2608_25376_gb300 import inputs, qpath
+    w = inputs.WORKLOADS[args.workload]
+    f = w["field"]()
+    kernel = {"rows": qpath.QP_KERNEL_STRUCTURED, "flat": qpath.QP_KERNEL_STRUCTURED_FLAT,
+              "dense": qpath.QP_KERNEL_DENSE}[args.profile_case]
+    flags = qpath.QP_STRUCTURED | (qpath.QP_DENSE if args.profile_case == "dense" else 0)
+    h = qpath.qp_build_qubo(f, flags=flags)
+    n = h.info["n"]
+    R = args.replicas or w["replicas"]
+    a, b = args.sweep_window
+    sc = qpath.schedule(w["n_sweeps"], sweep_begin=a, sweep_end=b)
+    st = torch.zeros((R, n), dtype=torch.uint8, device="cuda")
+    E = torch.zeros(R, dtype=torch.int64, device="cuda")
+    best = torch.zeros(R, dtype=torch.int64, device="cuda")
+    times = []
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        qpath.qp_anneal_ex(h, R, sc, w["seed"], None, st, E, best, kernel=kernel,
+                           replicas_per_cta=args.replicas_per_cta, stream=torch.cuda.current_stream())
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    C = h.info["C"]
+    print(json.dumps({"profile_case": args.profile_case, "workload": args.workload, "replicas": R,
+                      "sweeps": [a, b], "ms": times, "attempts": R * (b - a) * (C - 1) ** 2}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -83,8 +83,10 @@ typedef struct {
 
 /* qp_build_qubo flags */
 enum { QP_DENSE = 1, QP_STRUCTURED = 2, QP_DIST_I16 = 4 };
-/* qp_anneal_opts.kernel */
-enum { QP_KERNEL_AUTO = 0, QP_KERNEL_DENSE = 1, QP_KERNEL_STRUCTURED = 2 };
+/* qp_anneal_opts.kernel.  STRUCTURED uses the row-parallel kernel for fields of
+ * up to 512 cells and the general one above; STRUCTURED_FLAT forces the general
+ * structured kernel (any field up to 4096 cells). */
+enum { QP_KERNEL_AUTO = 0, QP_KERNEL_DENSE = 1, QP_KERNEL_STRUCTURED = 2, QP_KERNEL_STRUCTURED_FLAT = 3 };
 
 typedef struct {
   int32_t kernel;            /* QP_KERNEL_*; AUTO = structured when built     */

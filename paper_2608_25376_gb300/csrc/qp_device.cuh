@@ -1,0 +1,59 @@
+// Device helpers shared by the sweep kernels: Philox4x32-10, the acceptance
+// test, warp reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qp {
+namespace dev {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of the 4x32 S-box with
+// the key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4 &u, int j) {
+  return j == 0 ? u.x : (j == 1 ? u.y : (j == 2 ? u.z : u.w));
+}
+
+__device__ __forceinline__ long long warp_sum64(long long v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Relative margin of the float acceptance estimate.  The estimate
+// v = 2^(32 - dE * log2(e)/T) carries a relative error below 1e-5: the product
+// dE * c and the subtraction round to 2^-24 relative on an exponent of at most
+// 64 in magnitude (3.8e-6 absolute, 2.7e-6 relative in 2^x), c = log2(e)/T is
+// rounded to float (1.9e-6), exp2f is within 2 ulp (2.4e-7) and u -> float
+// rounds to 6e-8.  The margin is 2^-12 = 2.4e-4, 40x that sum.
+constexpr float kAcceptMargin = 1.0f / 4096.0f;
+
+// Proposal with 1 <= dE < len: accept iff u < thr[dE], thr[dE] =
+// floor(2^32 exp(-dE/T)) from the host table.  When u lies outside the band
+// v(1 -/+ margin) -/+ 2 around the float estimate the answer is the table's
+// (u < v(1-m) - 2 implies u < V - 1, hence u < floor(V); u > v(1+m) + 2
+// implies u >= floor(V)); inside the band the table itself is read.
+__device__ __forceinline__ bool accept_draw(uint32_t u, int dE, float c, const uint32_t *thr) {
+  const float v = exp2f(32.0f - (float)dE * c);
+  const float uf = __uint2float_rn(u);
+  if (uf < fmaf(v, -kAcceptMargin, v) - 2.0f) return true;
+  if (uf > fmaf(v, kAcceptMargin, v) + 2.0f) return false;
+  return u < __ldg(thr + dE);
+}
+
+}  // namespace dev
+}  // namespace qp

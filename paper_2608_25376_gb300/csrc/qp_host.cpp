@@ -134,7 +134,7 @@ struct SchedKey {
 };
 
 struct SchedEntry {
-  DevBuf thr, off, len;
+  DevBuf thr, off, len, c;
   DeviceSchedule view;
 };
 
@@ -158,10 +158,14 @@ qp_status device_schedule(const qp_schedule &sc, DeviceSchedule *out) {
   auto e = std::make_unique<SchedEntry>();
   std::vector<int64_t> off(sc.n_sweeps);
   std::vector<int32_t> len(sc.n_sweeps);
+  std::vector<float> cf(sc.n_sweeps);
   std::vector<uint32_t> all, tab;
+  const double log2e = 1.0 / std::log(2.0);
   int32_t max_len = 0;
   for (int s = 0; s < sc.n_sweeps; ++s) {
-    build_thresholds(temperature(sc, s), tab);
+    const double T = temperature(sc, s);
+    build_thresholds(T, tab);
+    cf[s] = (float)(log2e / T);
     off[s] = (int64_t)all.size();
     len[s] = (int32_t)tab.size();
     max_len = std::max(max_len, len[s]);
@@ -170,12 +174,15 @@ qp_status device_schedule(const qp_schedule &sc, DeviceSchedule *out) {
   QP_TRY(e->thr.ensure(all.size() * 4));
   QP_TRY(e->off.ensure(off.size() * 8));
   QP_TRY(e->len.ensure(len.size() * 4));
+  QP_TRY(e->c.ensure(cf.size() * 4));
+  QP_CU(cudaMemcpy(e->c.p, cf.data(), cf.size() * 4, cudaMemcpyHostToDevice));
   QP_CU(cudaMemcpy(e->thr.p, all.data(), all.size() * 4, cudaMemcpyHostToDevice));
   QP_CU(cudaMemcpy(e->off.p, off.data(), off.size() * 8, cudaMemcpyHostToDevice));
   QP_CU(cudaMemcpy(e->len.p, len.data(), len.size() * 4, cudaMemcpyHostToDevice));
   e->view.thr = e->thr.as<uint32_t>();
   e->view.off = e->off.as<int64_t>();
   e->view.len = e->len.as<int32_t>();
+  e->view.c = e->c.as<float>();
   e->view.n_sweeps = sc.n_sweeps;
   e->view.max_len = max_len;
   e->view.total = (int64_t)all.size();
@@ -437,9 +444,11 @@ extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc
     return fail(QP_EINVAL, "replica_offset out of range");
   int kernel = o.kernel;
   if (kernel == QP_KERNEL_AUTO) kernel = h->path ? QP_KERNEL_STRUCTURED : QP_KERNEL_DENSE;
-  if (kernel == QP_KERNEL_STRUCTURED && !h->path) return fail(QP_EINVAL, "no structured form in this handle");
+  if ((kernel == QP_KERNEL_STRUCTURED || kernel == QP_KERNEL_STRUCTURED_FLAT) && !h->path)
+    return fail(QP_EINVAL, "no structured form in this handle");
   if (kernel == QP_KERNEL_DENSE && !h->has_dense) return fail(QP_EINVAL, "handle was built without QP_DENSE");
-  if (kernel != QP_KERNEL_STRUCTURED && kernel != QP_KERNEL_DENSE) return fail(QP_EINVAL, "unknown kernel %d", kernel);
+  if (kernel != QP_KERNEL_STRUCTURED && kernel != QP_KERNEL_DENSE && kernel != QP_KERNEL_STRUCTURED_FLAT)
+    return fail(QP_EINVAL, "unknown kernel %d", kernel);
   if (o.replicas_per_cta < 0 || o.replicas_per_cta > kMaxWarpsPerCta)
     return fail(QP_EINVAL, "replicas_per_cta must be in [0, %d]", kMaxWarpsPerCta);
 
@@ -469,7 +478,7 @@ extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc
   const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
 
   LaunchInfo info;
-  if (kernel == QP_KERNEL_STRUCTURED) {
+  if (kernel == QP_KERNEL_STRUCTURED || kernel == QP_KERNEL_STRUCTURED_FLAT) {
     int W = o.replicas_per_cta ? o.replicas_per_cta : 4;
     StructArgs a{};
     a.C = h->C; a.Cp = h->Cp; a.start = h->start; a.A = h->A; a.B = h->B;
@@ -477,8 +486,16 @@ extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc
     a.R = R; a.rep_offset = o.replica_offset;
     a.sweep_begin = sc->sweep_begin; a.sweep_end = sc->sweep_end;
     a.key0 = key0; a.key1 = key1;
-    a.thr = sched.thr; a.thr_off = sched.off; a.thr_len = sched.len;
+    a.thr = sched.thr; a.thr_off = sched.off; a.thr_len = sched.len; a.thr_c = sched.c;
     a.init = init_d; a.states_out = st_d; a.E_out = e_d; a.best_out = b_d; a.acc_out = a_d;
+    if (kernel == QP_KERNEL_STRUCTURED) {
+      int Wr = W;
+      while (Wr > 1 && !rows_supported(h->C, h->d_i16, Wr)) --Wr;
+      if (rows_supported(h->C, h->d_i16, Wr)) {
+        QP_CU(launch_rows(a, h->d_i16, Wr, st, &info));
+        goto launched;
+      }
+    }
     a.nw_pad = (int32_t)structured_gstate_words(h->C);
     const bool want_smem = structured_state_fits_smem(h->C, h->d_i16, W) &&
                            4 * structured_gstate_words(h->C) <= 8 * 1024;
@@ -496,7 +513,7 @@ extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc
     a.R = R; a.rep_offset = o.replica_offset;
     a.sweep_begin = sc->sweep_begin; a.sweep_end = sc->sweep_end;
     a.key0 = key0; a.key1 = key1;
-    a.thr = sched.thr; a.thr_off = sched.off; a.thr_len = sched.len;
+    a.thr = sched.thr; a.thr_off = sched.off; a.thr_len = sched.len; a.thr_c = sched.c;
     a.init = init_d; a.states_out = st_d; a.E_out = e_d; a.best_out = b_d; a.acc_out = a_d;
     if (!dense_h_fits_smem(h->n, a.C, W)) {
       QP_TRY(h->hbuf.ensure((size_t)R * h->np * 4));
@@ -504,6 +521,7 @@ extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc
     }
     QP_CU(launch_dense(a, h->S_i16, W, st, &info));
   }
+launched:
   if (st_host) QP_CU(cudaMemcpyAsync(states_out, st_d, (size_t)R * n, cudaMemcpyDeviceToHost, st));
   if (e_host) QP_CU(cudaMemcpyAsync(energies_out, e_d, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
   if (b_host) QP_CU(cudaMemcpyAsync(best_out, b_d, (size_t)R * 8, cudaMemcpyDeviceToHost, st));

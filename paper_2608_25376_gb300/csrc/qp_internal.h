@@ -20,6 +20,7 @@ struct DeviceSchedule {
   const uint32_t *thr = nullptr;
   const int64_t *off = nullptr;
   const int32_t *len = nullptr;
+  const float *c = nullptr;  // log2(e) / T_s, rounded to float
   int32_t n_sweeps = 0;
   int32_t max_len = 0;
   int64_t total = 0;
@@ -35,6 +36,7 @@ struct StructArgs {
   const uint32_t *thr;
   const int64_t *thr_off;
   const int32_t *thr_len;
+  const float *thr_c;
   const uint8_t *init;       // R x n or null
   uint8_t *states_out;       // R x n
   int64_t *E_out, *best_out, *acc_out;  // best/acc may be null
@@ -56,6 +58,7 @@ struct DenseArgs {
   const uint32_t *thr;
   const int64_t *thr_off;
   const int32_t *thr_len;
+  const float *thr_c;
   const uint8_t *init;
   uint8_t *states_out;
   int64_t *E_out, *best_out, *acc_out;
@@ -74,6 +77,10 @@ cudaError_t launch_structured(const StructArgs &a, bool d_i16, int warps_per_cta
                               cudaStream_t st, LaunchInfo *info);
 size_t structured_gstate_words(int C);  // nw_pad for the global-state layout
 bool structured_state_fits_smem(int C, bool d_i16, int warps_per_cta);
+// Row-parallel structured kernel (qp_sweep_rows.cu), fields of up to 512 cells.
+bool rows_supported(int C, bool d_i16, int warps_per_cta);
+cudaError_t launch_rows(const StructArgs &a, bool d_i16, int warps_per_cta, cudaStream_t st,
+                        LaunchInfo *info);
 cudaError_t launch_dense(const DenseArgs &a, bool s_i16, int warps_per_cta, cudaStream_t st,
                          LaunchInfo *info);
 bool dense_h_fits_smem(int64_t n, int C, int warps_per_cta);

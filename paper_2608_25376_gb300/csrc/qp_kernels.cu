@@ -15,39 +15,19 @@
 // draw independent of when (or whether) it is computed.
 #include <climits>
 
+#include "qp_device.cuh"
 #include "qp_internal.h"
 
 namespace qp {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
+using dev::kFull;
+using dev::philox4x32_10;
+using dev::warp_sum64;
+using dev::word_of;
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
-
-// Philox4x32-10 (Salmon et al., SC'11): ten rounds of the 4x32 S-box with
-// the key bumped by the Weyl constants between rounds.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int i = 0; i < 10; ++i) {
-    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
-  }
-  return c;
-}
-
-__device__ __forceinline__ uint32_t word_of(const uint4 &u, int j) {
-  return j == 0 ? u.x : (j == 1 ? u.y : (j == 2 ? u.z : u.w));
-}
-
-__device__ __forceinline__ long long warp_sum64(long long v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
 
 // Bits of state word w that fall in [kb, ke); requires (w<<5) < ke and
 // (w<<5) + 32 > kb.
@@ -201,6 +181,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32)
   for (int s = a.sweep_begin; s < a.sweep_end; ++s) {
     const uint32_t *thr = a.thr + a.thr_off[s];
     const int len = a.thr_len[s];
+    const float cT = a.thr_c[s];
     for (int t = 1; t < C; ++t) {
       int nh = collect_hot(st, (t - 1) * C, C, hot, 0, lane);
       if (t + 1 < C) nh = collect_hot(st, (t + 1) * C, C, hot, nh, lane);
@@ -258,7 +239,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32)
           }
 #pragma unroll
           for (int j = 0; j < 4; ++j)
-            if (((need >> j) & 1) && word_of(u, j) < __ldg(thr + dE[j])) accm |= 1 << j;
+            if (((need >> j) & 1) && dev::accept_draw(word_of(u, j), dE[j], cT, thr)) accm |= 1 << j;
           const uint32_t bal = __ballot_sync(kFull, accm != 0);
           if (bal == 0) break;
           const int L = __ffs(bal) - 1;
@@ -438,6 +419,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_sweep_dense(const Dens
   for (int s = a.sweep_begin; s < a.sweep_end; ++s) {
     const uint32_t *thr = a.thr + a.thr_off[s];
     const int len = a.thr_len[s];
+    const float cT = a.thr_c[s];
     int pos = 0;
     for (int m0 = 0; m0 < nblk; m0 += 32) {
       const int m = m0 + lane;
@@ -474,7 +456,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_sweep_dense(const Dens
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-          if (((need >> j) & 1) && word_of(u, j) < __ldg(thr + dE[j])) accm |= 1 << j;
+          if (((need >> j) & 1) && dev::accept_draw(word_of(u, j), dE[j], cT, thr)) accm |= 1 << j;
         const uint32_t bal = __ballot_sync(kFull, accm != 0);
         if (bal == 0) break;
         const int L = __ffs(bal) - 1;

@@ -1,0 +1,498 @@
+// Row-parallel structured sweep for fields of up to 512 cells (sm_103a).
+//
+// One warp anneals one replica.  The sweep proposes x_{t,i} for t = 1..C-1 and
+// every cell i != s in increasing i, exactly as the sequential chain does.
+// Lane L owns the columns i = 128c + 4L + j (j = 0..3, chunk c < NCH) for the
+// whole run, so everything indexed by column lives in its registers:
+//   tAc[c][j]  2A times the column sums sum_t x_{t,i} (Eq. 4),
+//   P, Cu, N   the distance fields F_u(i) = sum_{h : x_{u,h} = 1} d_{h,i} of
+//              rows t-1, t and t+1 (Eq. 3), rotated from row to row; an accepted
+//              flip in row t adds one row of d to Cu, and row t+1's field is the
+//              d row of its single hot cell (cached per row) or, when the row
+//              does not hold exactly one cell, a scan of its bits.
+// With r the row-t sum and c_i the column sum (both including x), Eq. 6 gives
+//   dE = base - 2A + 2A r          (x = 0)
+//   dE = 6A - base - 2A r          (x = 1),     base = B (F_{t-1} + F_{t+1})(i) + 2A c_i.
+// A row chunk (128 proposals) is first tested as a whole: a proposal matters
+// only if dE <= 0 or 1 <= dE < len_s (one add and one unsigned compare), and
+// at low temperature most rows have none, so they cost a few instructions per
+// proposal.  Otherwise the warp evaluates the chunk against the current state,
+// a ballot finds the first accepted proposal, the flip is applied and
+// evaluation resumes after it: exactly the sequential order.  The spins are a bitset per row (Cw = ceil(C/32) words) in
+// shared memory; the distance matrix is staged in shared memory (widened to
+// int32 when that fits) or read from L2.
+//
+// The draw of x_{t,i} is word k&3 of Philox4x32-10(counter = (k>>2, sweep,
+// replica, tag)), k = t*C + i; a lane's four proposals span one or two counter
+// blocks, each computed only when one of its proposals has 1 <= dE < len_s.
+#include <climits>
+
+#include "qp_device.cuh"
+#include "qp_internal.h"
+
+namespace qp {
+namespace {
+
+using namespace dev;
+
+__host__ __device__ constexpr size_t align16r(size_t x) { return (x + 15) & ~size_t(15); }
+
+// d modes: 0 = global memory (DT), 1 = shared memory (DT), 2 = shared memory widened to int32
+template <typename DT, int DMODE>
+__device__ __forceinline__ void drow4(const void *d, int Cp, int h, int i, bool ok, int (&v)[4]) {
+  v[0] = v[1] = v[2] = v[3] = 0;
+  if (!ok) return;
+  if (DMODE == 2) {
+    const int4 q = *reinterpret_cast<const int4 *>(static_cast<const int *>(d) + (size_t)h * Cp + i);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else if (sizeof(DT) == 2) {
+    const uint2 *p = reinterpret_cast<const uint2 *>(static_cast<const DT *>(d) + (size_t)h * Cp + i);
+    const uint2 q = DMODE == 1 ? *p : __ldg(p);
+    v[0] = (int)(short)(q.x & 0xFFFFu);
+    v[1] = (int)q.x >> 16;
+    v[2] = (int)(short)(q.y & 0xFFFFu);
+    v[3] = (int)q.y >> 16;
+  } else {
+    const int4 *p = reinterpret_cast<const int4 *>(static_cast<const DT *>(d) + (size_t)h * Cp + i);
+    const int4 q = DMODE == 1 ? *p : __ldg(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  }
+}
+
+template <typename DT, int NCH, int DMODE>
+__device__ __forceinline__ void add_drow(const void *d, int Cp, int C, int h, int lane, int dlt,
+                                         int (&F)[NCH][4]) {
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    const int i = 128 * c + 4 * lane;
+    int v[4];
+    drow4<DT, DMODE>(d, Cp, h, i, i < C, v);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) F[c][j] += dlt * v[j];
+  }
+}
+
+// F += sum over the set bits h of one row of d[h][.]; returns the number of bits
+// and, in *one, the cell when there is exactly one (else -1).
+template <typename DT, int NCH, int DMODE>
+__device__ __forceinline__ int scan_row_field(const uint32_t *row, int Cw, const void *d, int Cp, int C,
+                                              int lane, int (&F)[NCH][4], int *one) {
+  const uint32_t word = lane < Cw ? row[lane] : 0u;
+  const int cnt = __reduce_add_sync(kFull, __popc(word));
+  uint32_t bal = __ballot_sync(kFull, word != 0u);
+  int last = -1;
+  while (bal) {
+    const int w = __ffs(bal) - 1;
+    bal &= bal - 1;
+    uint32_t wd = __shfl_sync(kFull, word, w);
+    while (wd) {
+      const int h = (w << 5) + __ffs(wd) - 1;
+      wd &= wd - 1;
+      last = h;
+      add_drow<DT, NCH, DMODE>(d, Cp, C, h, lane, 1, F);
+    }
+  }
+  *one = cnt == 1 ? last : -1;
+  return cnt;
+}
+
+// The single hot cell of a row, or -1 if the row does not hold exactly one.
+__device__ __forceinline__ int row_single(const uint32_t *row, int Cw, int lane) {
+  const uint32_t word = lane < Cw ? row[lane] : 0u;
+  const int cnt = __reduce_add_sync(kFull, __popc(word));
+  if (cnt != 1) return -1;
+  const uint32_t bal = __ballot_sync(kFull, word != 0u);
+  const int w = __ffs(bal) - 1;
+  const uint32_t wd = __shfl_sync(kFull, word, w);
+  return (w << 5) + __ffs(wd) - 1;
+}
+
+template <int NCH>
+__device__ __forceinline__ void zero(int (&F)[NCH][4]) {
+#pragma unroll
+  for (int c = 0; c < NCH; ++c)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) F[c][j] = 0;
+}
+
+__device__ __forceinline__ int sel4(const int (&v)[4], int j) {
+  return j == 0 ? v[0] : (j == 1 ? v[1] : (j == 2 ? v[2] : v[3]));
+}
+
+// The proposals of one 128-wide row chunk when at least one of them can be
+// accepted or needs a draw: evaluate against the current row sum, take the
+// first accepted one, apply it, resume after it.  Returns whether any flip was
+// applied.
+template <typename DT, int NCH, int DMODE>
+__device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int (&base)[4], int &xnc, int validc,
+                                       int (&tAc)[4], int &rt, int (&Cu)[NCH][4], uint32_t *row, long long &E,
+                                       long long &acc, int &viol, const void *d, int Cp, int C, int lane, int twoA,
+                                       int len, unsigned lenm1, float cT, const uint32_t *thr, uint32_t rg,
+                                       uint32_t key0, uint32_t key1) {
+  const int ib = 128 * c + 4 * lane;
+  const int delta = tC & 3;
+  int cand = validc;
+  bool h0 = false, h1 = false, flipped = false;
+  uint4 u0 = make_uint4(0, 0, 0, 0), u1 = make_uint4(0, 0, 0, 0);
+  while (true) {
+    const int k0 = twoA * (rt - 1), k1 = twoA * (3 - rt);
+    int accm = 0, need = 0, dE[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      dE[j] = ((xnc >> j) & 1) ? k1 - base[j] : base[j] + k0;
+      const unsigned dm1 = (unsigned)(dE[j] - 1);
+      accm |= (int)(dm1 >> 31) << j;   // dE <= 0
+      need |= (int)(dm1 < lenm1) << j;  // 1 <= dE < len
+    }
+    accm &= cand;
+    need &= cand;
+    if (__ballot_sync(kFull, need)) {
+      // lane L's proposals lie in counter blocks b0 and (when delta != 0) b0 + 1,
+      // which is lane L+1's b0: every lane computes its own block once and
+      // takes the next one from its right neighbour; lane 31 computes its
+      // second block itself when it needs it.
+      const int m0 = (1 << (4 - delta)) - 1;
+      const uint32_t b0 = (uint32_t)((tC + ib) >> 2);
+      if (!h0) {
+        u0 = philox4x32_10(make_uint4(b0, (uint32_t)s, rg, kRngTag), key0, key1);
+        u1.x = __shfl_down_sync(kFull, u0.x, 1);
+        u1.y = __shfl_down_sync(kFull, u0.y, 1);
+        u1.z = __shfl_down_sync(kFull, u0.z, 1);
+        u1.w = __shfl_down_sync(kFull, u0.w, 1);
+        h0 = true;
+      }
+      if (lane == 31 && (need & ~m0) && !h1) {
+        u1 = philox4x32_10(make_uint4(b0 + 1, (uint32_t)s, rg, kRngTag), key0, key1);
+        h1 = true;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if ((need >> j) & 1) {
+          const int wsel = (delta + j) & 3;
+          const uint32_t u = (j < 4 - delta) ? word_of(u0, wsel) : word_of(u1, wsel);
+          if (accept_draw(u, dE[j], cT, thr)) accm |= 1 << j;
+        }
+      }
+    }
+    const uint32_t bal = __ballot_sync(kFull, accm);
+    if (bal == 0) break;
+    const int L = __ffs(bal) - 1;
+    const int jl = accm ? __ffs(accm) - 1 : 0;
+    const int xl = (xnc >> jl) & 1;
+    const int tc = sel4(tAc, jl);
+    const int pk0 = jl | (xl << 2) | ((tc == twoA) << 3) | ((tc + (1 - 2 * xl) * twoA == twoA) << 4);
+    const int de = __shfl_sync(kFull, sel4(dE, jl), L);
+    const int pk = __shfl_sync(kFull, pk0, L);
+    const int jj = pk & 3, dlt = 1 - 2 * ((pk >> 2) & 1);
+    E += de;
+    ++acc;
+    rt += dlt;
+    viol += ((pk >> 4) & 1 ? 0 : 1) - ((pk >> 3) & 1 ? 0 : 1);
+    flipped = true;
+    if (lane == L) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j == jj) tAc[j] += dlt * twoA;
+      xnc ^= 1 << jj;
+      row[4 * c + (L >> 3)] ^= 1u << (4 * (L & 7) + jj);
+    }
+    add_drow<DT, NCH, DMODE>(d, Cp, C, 128 * c + 4 * L + jj, lane, dlt, Cu);
+    cand &= lane < L ? 0 : (lane > L ? 0xF : (0xF << (jj + 1)) & 0xF);
+    __syncwarp();
+  }
+  return flipped;
+}
+
+// Widest rows (NCH = 4) keep three 16-register fields per lane: they get up to
+// 255 registers by capping the CTA at 8 replicas.
+template <int NCH>
+constexpr int rows_max_warps() { return NCH >= 4 ? 8 : kMaxWarpsPerCta; }
+
+template <typename DT, int NCH, int DMODE>
+__global__ void __launch_bounds__(rows_max_warps<NCH>() * 32) k_sweep_rows(const StructArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const int C = a.C, Cp = a.Cp, s0 = a.start, A = a.A, B = a.B;
+  const int twoA = 2 * A;
+  const int Cw = (C + 31) >> 5;
+  const int n = C * C;
+  unsigned char *p = smem;
+  const void *d = a.d;
+  if (DMODE == 1) {
+    const int nv = (int)((size_t)C * Cp * sizeof(DT) / 16);
+    const int4 *src = static_cast<const int4 *>(a.d);
+    int4 *dst = reinterpret_cast<int4 *>(p);
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) dst[v] = __ldg(src + v);
+    d = p;
+    p += align16r((size_t)C * Cp * sizeof(DT));
+  } else if (DMODE == 2) {
+    const DT *src = static_cast<const DT *>(a.d);
+    int *dst = reinterpret_cast<int *>(p);
+    for (int e = threadIdx.x; e < C * Cp; e += blockDim.x) dst[e] = (int)__ldg(src + e);
+    d = p;
+    p += align16r((size_t)C * Cp * 4);
+  }
+  const size_t per_warp = 4 * (size_t)a.nw_pad + align16r(2 * (size_t)C);
+  uint32_t *st = reinterpret_cast<uint32_t *>(p + warp * per_warp);
+  int16_t *hot1 = reinterpret_cast<int16_t *>(p + warp * per_warp + 4 * (size_t)a.nw_pad);
+  __syncthreads();
+  const int r = blockIdx.x * W + warp;
+  if (r >= a.R) return;  // no CTA-wide barrier after this point
+  const uint32_t rg = (uint32_t)(a.rep_offset + r);
+
+  // ---- initial state: given or all zero; row 0 and column s clamped (x_{0,s} = 1)
+  const uint8_t *init = a.init ? a.init + (size_t)r * n : nullptr;
+  for (int e = lane; e < C * Cw; e += 32) {
+    const int t = e / Cw, w = e - t * Cw;
+    uint32_t word = 0;
+    if (t == 0) {
+      if ((s0 >> 5) == w) word = 1u << (s0 & 31);
+    } else if (init) {
+      for (int b = 0; b < 32; ++b) {
+        const int i = (w << 5) + b;
+        if (i < C && i != s0 && init[(size_t)t * C + i]) word |= 1u << b;
+      }
+    }
+    st[e] = word;
+  }
+  __syncwarp();
+
+  // ---- column sums, per-row single cells, penalties and H_dist (Eqs. 3-6)
+  int cs[NCH][4];
+  zero<NCH>(cs);
+  int tAc[NCH][4];  // 2A * column sum, kept through the sweeps
+  int validc[NCH];
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    validc[c] = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = 128 * c + 4 * lane + j;
+      if (i < C && i != s0) validc[c] |= 1 << j;
+    }
+  }
+  long long hd = 0, pen_rows = 0;
+  int viol = 0;
+  {
+    int Fn[NCH][4];
+    for (int t = 0; t < C; ++t) {
+      const uint32_t *row = st + t * Cw;
+      int rsum = 0, xb[NCH];
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) {
+        const int ib = 128 * c + 4 * lane;
+        xb[c] = ib < C ? (int)((row[4 * c + (lane >> 3)] >> (4 * (lane & 7))) & 0xFu) : 0;
+        rsum += __popc(xb[c]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cs[c][j] += (xb[c] >> j) & 1;
+      }
+      rsum = __reduce_add_sync(kFull, rsum);
+      pen_rows += (long long)(1 - rsum) * (1 - rsum);
+      viol += rsum != 1;
+      const int h1 = row_single(row, Cw, lane);
+      if (lane == 0) hot1[t] = (int16_t)h1;
+      if (t + 1 < C) {
+        zero<NCH>(Fn);
+        int one;
+        scan_row_field<DT, NCH, DMODE>(st + (t + 1) * Cw, Cw, d, Cp, C, lane, Fn, &one);
+#pragma unroll
+        for (int c = 0; c < NCH; ++c)
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if ((xb[c] >> j) & 1) hd += Fn[c][j];
+      }
+    }
+  }
+  __syncwarp();
+  long long pen_cols = 0;
+  int viol_cols = 0;
+#pragma unroll
+  for (int c = 0; c < NCH; ++c)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (128 * c + 4 * lane + j < C) {
+        pen_cols += (long long)(1 - cs[c][j]) * (1 - cs[c][j]);
+        viol_cols += cs[c][j] != 1;
+      }
+  long long E = (long long)B * warp_sum64(hd) + (long long)A * (pen_rows + warp_sum64(pen_cols));
+  viol += __reduce_add_sync(kFull, viol_cols);
+  long long best = LLONG_MAX, acc = 0;
+#pragma unroll
+  for (int c = 0; c < NCH; ++c)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) tAc[c][j] = twoA * cs[c][j];
+
+  // ---- sweeps
+  for (int s = a.sweep_begin; s < a.sweep_end; ++s) {
+    const uint32_t *thr = a.thr + a.thr_off[s];
+    const int len = a.thr_len[s];
+    const unsigned lenm1 = (unsigned)(len - 1);
+    const unsigned hi = 0x80000000u - lenm1;
+    const float cT = a.thr_c[s];
+    int P[NCH][4], Cu[NCH][4], N[NCH][4], Nn[NCH][4];
+    zero<NCH>(P);
+    zero<NCH>(Cu);
+    zero<NCH>(Nn);
+    add_drow<DT, NCH, DMODE>(d, Cp, C, s0, lane, 1, P);  // row 0 holds only the start cell
+    {
+      const int h = hot1[1];
+      if (h >= 0) add_drow<DT, NCH, DMODE>(d, Cp, C, h, lane, 1, Cu);
+      else { int one; scan_row_field<DT, NCH, DMODE>(st + Cw, Cw, d, Cp, C, lane, Cu, &one); }
+    }
+    // Row t needs F_{t+1} and its own bits; both are loaded one row ahead
+    // (neither can change before row t is processed), and the single-cell
+    // cache two rows ahead.
+    if (C > 2) {
+      const int h = hot1[2];
+      if (h >= 0) add_drow<DT, NCH, DMODE>(d, Cp, C, h, lane, 1, Nn);
+      else { int one; scan_row_field<DT, NCH, DMODE>(st + 2 * Cw, Cw, d, Cp, C, lane, Nn, &one); }
+    }
+    int h2 = C > 3 ? hot1[3] : -1;
+    int xnn[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c)
+      xnn[c] = 128 * c + 4 * lane < C ? (int)((st[Cw + 4 * c + (lane >> 3)] >> (4 * (lane & 7))) & 0xFu) : 0;
+    for (int t = 1; t < C; ++t) {
+      uint32_t *row = st + t * Cw;
+      int xn[NCH];
+      int rt = 0;
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) {
+        xn[c] = xnn[c];
+        rt += __popc(xn[c]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          N[c][j] = Nn[c][j];
+          Nn[c][j] = 0;
+        }
+      }
+      if (t + 2 < C) {
+        if (h2 >= 0) add_drow<DT, NCH, DMODE>(d, Cp, C, h2, lane, 1, Nn);
+        else { int one; scan_row_field<DT, NCH, DMODE>(row + 2 * Cw, Cw, d, Cp, C, lane, Nn, &one); }
+      }
+      h2 = t + 3 < C ? hot1[t + 3] : -1;
+#pragma unroll
+      for (int c = 0; c < NCH; ++c)
+        xnn[c] = (t + 1 < C && 128 * c + 4 * lane < C)
+                     ? (int)((row[Cw + 4 * c + (lane >> 3)] >> (4 * (lane & 7))) & 0xFu) : 0;
+      rt = __reduce_add_sync(kFull, rt);
+      const int rt0 = rt;
+      bool flipped = false;
+      const int tC = t * C;
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) {
+        if (128 * c >= C) break;
+        // base = B f + 2A c_i;  dE = base + 2A(r-1) (x = 0),  2A(3-r) - base (x = 1)
+        int base[4];
+        unsigned hit = 0;
+        {
+          const int k0 = twoA * (rt - 1), k1 = twoA * (3 - rt);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            base[j] = B * (P[c][j] + N[c][j]) + tAc[c][j];
+            const int de = ((xn[c] >> j) & 1) ? k1 - base[j] : base[j] + k0;
+            // dE <= 0 or 1 <= dE < len  <=>  (dE - 1 - (len - 1)) mod 2^32 >= 2^31 - (len - 1)
+            hit |= (unsigned)((unsigned)(de - 1) - lenm1 >= hi) << j;
+          }
+        }
+        if (__any_sync(kFull, hit & validc[c]))
+          flipped |= row_chunk<DT, NCH, DMODE>(c, t, s, tC, base, xn[c], validc[c], tAc[c], rt, Cu, row, E, acc,
+                                               viol, d, Cp, C, lane, twoA, len, lenm1, cT, thr, rg, a.key0, a.key1);
+      }
+      viol += (rt != 1) - (rt0 != 1);
+      if (flipped) {
+        const int h1v = row_single(row, Cw, lane);
+        if (lane == 0) hot1[t] = (int16_t)h1v;
+        __syncwarp();
+      }
+#pragma unroll
+      for (int c = 0; c < NCH; ++c)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          P[c][j] = Cu[c][j];
+          Cu[c][j] = N[c][j];
+        }
+    }
+    if (viol == 0 && E < best) best = E;
+  }
+
+  // ---- outputs
+  uint8_t *out = a.states_out + (size_t)r * n;
+  for (int e = lane; e < n; e += 32) {
+    const int t = e / C, i = e - t * C;
+    out[e] = (uint8_t)((st[t * Cw + (i >> 5)] >> (i & 31)) & 1u);
+  }
+  if (lane == 0) {
+    a.E_out[r] = E;
+    if (a.best_out) a.best_out[r] = best;
+    if (a.acc_out) a.acc_out[r] = acc;
+  }
+}
+
+constexpr size_t kSmemLimitRows = 227 * 1024;
+
+template <typename DT, int NCH, int DMODE>
+cudaError_t launch_r(const StructArgs &a, int W, size_t smem, cudaStream_t st) {
+  auto k = k_sweep_rows<DT, NCH, DMODE>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<(a.R + W - 1) / W, W * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename DT, int NCH>
+cudaError_t launch_r2(const StructArgs &a, int dmode, int W, size_t smem, cudaStream_t st) {
+  if (dmode == 2) return launch_r<DT, NCH, 2>(a, W, smem, st);
+  if (dmode == 1) return launch_r<DT, NCH, 1>(a, W, smem, st);
+  return launch_r<DT, NCH, 0>(a, W, smem, st);
+}
+
+}  // namespace
+
+size_t rows_state_words(int C) {
+  const int Cw = (C + 31) / 32;
+  return (size_t)(C * Cw + 3) / 4 * 4;
+}
+
+// Shared memory of the row kernel: d (mode 1: as stored, mode 2: widened to
+// int32) + per replica its row bitsets and single-cell cache.
+size_t rows_smem(int C, bool d_i16, int W, int dmode) {
+  const int Cp = (C + 7) / 8 * 8;
+  size_t dbytes = 0;
+  if (dmode == 1) dbytes = align16r((size_t)C * Cp * (d_i16 ? 2 : 4));
+  if (dmode == 2) dbytes = align16r((size_t)C * Cp * 4);
+  return dbytes + (size_t)W * (4 * rows_state_words(C) + align16r(2 * (size_t)C));
+}
+
+bool rows_supported(int C, bool d_i16, int W) {
+  const int wmax = C <= 256 ? kMaxWarpsPerCta : 8;
+  return C <= 512 && W >= 1 && W <= wmax && rows_smem(C, d_i16, W, 0) <= kSmemLimitRows;
+}
+
+cudaError_t launch_rows(const StructArgs &a_in, bool d_i16, int W, cudaStream_t st, LaunchInfo *info) {
+  StructArgs a = a_in;
+  a.nw_pad = (int32_t)rows_state_words(a.C);
+  if (!rows_supported(a.C, d_i16, W)) return cudaErrorInvalidValue;
+  int dmode = 0;
+  if (rows_smem(a.C, d_i16, W, 2) <= kSmemLimitRows) dmode = 2;
+  else if (rows_smem(a.C, d_i16, W, 1) <= kSmemLimitRows) dmode = 1;
+  const size_t smem = rows_smem(a.C, d_i16, W, dmode);
+  if (smem > kSmemLimitRows) return cudaErrorInvalidValue;
+  const int NCH = a.C <= 128 ? 1 : (a.C <= 256 ? 2 : 4);
+  if (info) {
+    info->warps_per_cta = W;
+    info->blocks = (a.R + W - 1) / W;
+    info->smem = smem;
+    info->variant = dmode == 2 ? "rows,d:smem32" : (dmode == 1 ? "rows,d:smem" : "rows,d:global");
+  }
+  if (d_i16) {
+    if (NCH == 1) return launch_r2<int16_t, 1>(a, dmode, W, smem, st);
+    if (NCH == 2) return launch_r2<int16_t, 2>(a, dmode, W, smem, st);
+    return launch_r2<int16_t, 4>(a, dmode, W, smem, st);
+  }
+  if (NCH == 1) return launch_r2<int32_t, 1>(a, dmode, W, smem, st);
+  if (NCH == 2) return launch_r2<int32_t, 2>(a, dmode, W, smem, st);
+  return launch_r2<int32_t, 4>(a, dmode, W, smem, st);
+}
+
+}  // namespace qp

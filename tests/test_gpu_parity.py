@@ -92,43 +92,74 @@ def test_build_matches_oracle(dev, orc, name, f):
 
 
 # ----------------------------------------------------------------- structured sweep
+STRUCT_KERNELS = [("rows", qpath.QP_KERNEL_STRUCTURED), ("flat", qpath.QP_KERNEL_STRUCTURED_FLAT)]
+
+
+@pytest.mark.parametrize("kname,kernel", STRUCT_KERNELS)
 @pytest.mark.parametrize("name,f", FIELDS)
-def test_structured_parity(dev, orc, name, f):
+def test_structured_parity(dev, orc, name, f, kname, kernel):
     P = problem(orc, f)
     R, S = (32, 300) if P.C <= 40 else (8, 60)
     h = qpath.qp_build_qubo(f)
     ref = orc.anneal_structured(P, R, S, seed=7)
-    assert_same(gpu_anneal(h, R, S, 7), ref)
+    assert_same(gpu_anneal(h, R, S, 7, kernel=kernel), ref)
 
 
-def test_structured_multichunk_global_state(dev, orc):
-    """C > 256 puts the spins in global memory and rows span several 128-wide
-    chunks with a ragged tail."""
+@pytest.mark.parametrize("kname,kernel", STRUCT_KERNELS)
+def test_structured_multichunk(dev, orc, kname, kernel):
+    """256 < C <= 512: rows span several 128-wide chunks with a ragged tail (the
+    row kernel's widest variant); the flat kernel keeps its spins in global
+    memory here."""
     f = inputs.obstacles(18, 18, 0.1, seed=8, start=5)
     P = problem(orc, f)
-    assert P.C > 256
+    assert 256 < P.C <= 512
     h = qpath.qp_build_qubo(f)
     ref = orc.anneal_structured(P, 3, 12, seed=3)
-    assert_same(gpu_anneal(h, 3, 12, 3), ref)
+    assert_same(gpu_anneal(h, 3, 12, 3, kernel=kernel), ref)
 
 
+def test_structured_above_512_cells_falls_back(dev, orc):
+    f = inputs.obstacles(24, 24, 0.05, seed=8)
+    P = problem(orc, f)
+    assert P.C > 512
+    h = qpath.qp_build_qubo(f)
+    ref = orc.anneal_structured(P, 2, 3, seed=3)
+    assert_same(gpu_anneal(h, 2, 3, 3), ref)
+
+
+@pytest.mark.parametrize("kname,kernel", STRUCT_KERNELS)
 @pytest.mark.parametrize("rpc", [1, 2, 3, 8, 16])
-def test_structured_replicas_per_cta(dev, orc, rpc):
+def test_structured_replicas_per_cta(dev, orc, rpc, kname, kernel):
     f = inputs.obstacles(7, 7, 0.15, seed=2)
     P = problem(orc, f)
     h = qpath.qp_build_qubo(f)
     ref = orc.anneal_structured(P, 21, 80, seed=11)
-    assert_same(gpu_anneal(h, 21, 80, 11, rpc=rpc), ref)
+    assert_same(gpu_anneal(h, 21, 80, 11, rpc=rpc, kernel=kernel), ref)
 
 
-def test_structured_int32_distances(dev, orc):
-    """B large enough that the dE bound still fits while scale forces int32 d."""
+@pytest.mark.parametrize("kname,kernel", STRUCT_KERNELS)
+def test_structured_hot_start(dev, orc, kname, kernel):
+    """Dense random initial states (many hot cells per row) at a high fixed
+    temperature: every draw path, many accepts per row."""
+    f = inputs.obstacles(9, 11, 0.1, seed=12, start=3)
+    P = problem(orc, f)
+    h = qpath.qp_build_qubo(f)
+    rng = np.random.default_rng(12)
+    R = 10
+    init = (rng.random((R, P.n)) < 0.4).astype(np.uint8)
+    ref = orc.anneal_structured(P, R, 30, seed=13, init_states=init, T0=5e4, T1=5e4)
+    assert_same(gpu_anneal(h, R, 30, 13, T0=5e4, T1=5e4, init=init, kernel=kernel), ref)
+
+
+@pytest.mark.parametrize("kname,kernel", STRUCT_KERNELS)
+def test_structured_int32_distances(dev, orc, kname, kernel):
+    """scale = 10000 forces int32 distances while the dE bound still fits."""
     f = inputs.obstacles(5, 5, 0.1, seed=4)
     P = orc.Problem(f.rows, f.cols, f.free_mask, f.start, scale=10000)
     assert P.max_d > 32767
     h = qpath.qp_build_qubo(f, scale=10000)
     ref = orc.anneal_structured(P, 16, 100, seed=2)
-    assert_same(gpu_anneal(h, 16, 100, 2), ref)
+    assert_same(gpu_anneal(h, 16, 100, 2, kernel=kernel), ref)
 
 
 def test_init_states_offset_seed_and_host_buffers(dev, orc):
@@ -183,12 +214,13 @@ def test_dense_path_parity_4x4_full_workload(dev, orc):
 
 
 @pytest.mark.parametrize("name,f", FIELDS[1:6])
-def test_dense_equals_structured_kernel(dev, orc, name, f):
+def test_dense_equals_structured_kernels(dev, orc, name, f):
     h = qpath.qp_build_qubo(f, flags=qpath.QP_DENSE | qpath.QP_STRUCTURED)
     a = gpu_anneal(h, 16, 200, 3, kernel=qpath.QP_KERNEL_DENSE)
-    b = gpu_anneal(h, 16, 200, 3, kernel=qpath.QP_KERNEL_STRUCTURED)
-    for x, y in zip(a, b):
-        assert (x == y).all()
+    for k in (qpath.QP_KERNEL_STRUCTURED, qpath.QP_KERNEL_STRUCTURED_FLAT):
+        b = gpu_anneal(h, 16, 200, 3, kernel=k)
+        for x, y in zip(a, b):
+            assert (x == y).all()
 
 
 @pytest.mark.parametrize("n", [5, 37, 300])
