@@ -154,6 +154,29 @@ qp_status qp_anneal_ex(qp_handle *h, int32_t replicas, const qp_schedule *sched,
                        int64_t *energies_out, int64_t *best_out, const qp_anneal_opts *opts,
                        void *cuda_stream);
 
+/* The structured anneal of qp_anneal_ex (same kernel as QP_KERNEL_STRUCTURED_FLAT,
+ * same results) without any allocation, for callers that cannot allocate
+ * device memory while they run: software that reserves all of its memory at
+ * start-up, code under an external memory manager that owns the GPU's memory,
+ * or a loop that cannot afford an allocation's latency.  The paper has no
+ * counterpart; this is a deployment entry point.
+ * The per-replica working state lives in a fixed 16 MiB array in the library's
+ * own device memory (held by every GPU that loads the library until exit):
+ * R * (ceil(C*C/32) + 1, rounded up to 4) * 4 bytes must fit, else QP_ERANGE.
+ * Every buffer (init_states, states_out, energies_out, best_out) must be
+ * device memory (QP_EINVAL otherwise); init_states and best_out may be NULL.
+ * The schedule's threshold tables must already exist on the device: one
+ * earlier qp_anneal/qp_anneal_ex call with the same n_sweeps, T0 and T1 builds
+ * them (QP_EINVAL otherwise).  The first call on each device looks up the
+ * array's device address; make that first call before any stream capture.
+ * Every call shares the one array, and each kernel rewrites the part it uses
+ * before reading it, so nothing carries over between calls; calls that overlap
+ * on the GPU (other streams, other threads) race on it and must be
+ * serialised by the caller.  Asynchronous on cuda_stream. */
+qp_status qp_anneal_noalloc(qp_handle *h, int32_t replicas, const qp_schedule *sched, uint64_t seed,
+                            const uint8_t *init_states, uint8_t *states_out, int64_t *energies_out,
+                            int64_t *best_out, int32_t replica_offset, void *cuda_stream);
+
 /* Algorithm 1 last step: the flight path of one state (n bytes, host or
  * device).  path_out[t] = cell id flown at step t (C int32, host), *length_out
  * = sum_t d(path[t], path[t+1]) (host).  QP_EINFEASIBLE if a row or column

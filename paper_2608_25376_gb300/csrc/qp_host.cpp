@@ -607,3 +607,38 @@ extern "C" void qp_destroy(qp_handle *h) {
 }
 
 extern "C" const char *qp_last_error(void) { return g_err.c_str(); }
+
+// --------------------------------------------------------------------------- lookups that never allocate
+namespace qp {
+
+bool handle_struct_view(const qp_handle *h, StructView *out) {
+  if (!h || !h->path) return false;
+  out->dev = h->dev;
+  out->C = h->C;
+  out->Cp = h->Cp;
+  out->start = h->start;
+  out->A = h->A;
+  out->B = h->B;
+  out->d = h->d_dev.p;
+  out->d_i16 = h->d_i16;
+  return true;
+}
+
+bool schedule_lookup(const qp_schedule &sc, DeviceSchedule *out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  SchedKey key{dev, sc.n_sweeps, 0, 0};
+  std::memcpy(&key.t0, &sc.T0, 8);
+  std::memcpy(&key.t1, &sc.T1, 8);
+  std::lock_guard<std::mutex> lk(g_sched_mu);
+  auto it = g_sched.find(key);
+  if (it == g_sched.end()) return false;
+  *out = it->second->view;
+  return true;
+}
+
+qp_status set_error(qp_status s, const char *msg) { return fail(s, "%s", msg); }
+
+bool device_pointer(const void *p) { return is_device_ptr(p); }
+
+}  // namespace qp

@@ -89,4 +89,17 @@ cudaError_t launch_build_dense(void *S, bool s_i16, int32_t np, int32_t C, const
 cudaError_t launch_decode(const uint8_t *states, int32_t R, int32_t C, const int32_t *d32,
                           int32_t *paths, int64_t *lengths, cudaStream_t st);
 
+// Read-only views used by the allocation-free entry point (qp_noalloc.cu);
+// none of these allocate.
+struct StructView {
+  int dev;
+  int32_t C, Cp, start, A, B;
+  const void *d;
+  bool d_i16;
+};
+bool handle_struct_view(const qp_handle *h, StructView *out);  // false for a generic QUBO
+bool schedule_lookup(const qp_schedule &sc, DeviceSchedule *out);  // false if never built here
+qp_status set_error(qp_status s, const char *msg);
+bool device_pointer(const void *p);
+
 }  // namespace qp

@@ -25,8 +25,8 @@ E_NONE = np.iinfo(np.int64).max
 
 # every entry point include/qpath.h declares
 SYMBOLS = ["qp_build_qubo", "qp_build_from_dense", "qp_qubo_info", "qp_export_dense", "qp_export_dist",
-           "qp_thresholds", "qp_anneal", "qp_anneal_ex", "qp_decode_path", "qp_decode_batch",
-           "qp_destroy", "qp_last_error"]
+           "qp_thresholds", "qp_anneal", "qp_anneal_ex", "qp_anneal_noalloc", "qp_decode_path",
+           "qp_decode_batch", "qp_destroy", "qp_last_error"]
 
 
 class QpError(RuntimeError):
@@ -73,6 +73,7 @@ def lib():
                 "qp_thresholds": [P(qp_schedule), i32, vp, i32, P(i32)],
                 "qp_anneal": [vp, i32, P(qp_schedule), u64, vp, vp, vp, vp, vp],
                 "qp_anneal_ex": [vp, i32, P(qp_schedule), u64, vp, vp, vp, vp, P(qp_anneal_opts), vp],
+                "qp_anneal_noalloc": [vp, i32, P(qp_schedule), u64, vp, vp, vp, vp, i32, vp],
                 "qp_decode_path": [vp, vp, vp, vp],
                 "qp_decode_batch": [vp, i32, vp, vp, vp, vp],
             }
@@ -206,6 +207,14 @@ def qp_anneal_ex(h: Handle, replicas, sched, seed, init_states, states_out, ener
     _check(lib().qp_anneal_ex(h.ptr, int(replicas), ct.byref(sched), ct.c_uint64(seed), _ptr(init_states),
                               _ptr(states_out), _ptr(energies_out), _ptr(best_out), ct.byref(o),
                               _stream(stream)))
+
+
+def qp_anneal_noalloc(h: Handle, replicas, sched, seed, init_states, states_out, energies_out, best_out=None,
+                      replica_offset=0, stream=None):
+    """The allocation-free structured anneal (device buffers only)."""
+    _check(lib().qp_anneal_noalloc(h.ptr, int(replicas), ct.byref(sched), ct.c_uint64(seed), _ptr(init_states),
+                                   _ptr(states_out), _ptr(energies_out), _ptr(best_out), int(replica_offset),
+                                   _stream(stream)))
 
 
 def qp_decode_path(h: Handle, state):
