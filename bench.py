@@ -79,8 +79,10 @@ def peaks():
 
 
 def kernel_source_hash():
+    """Hash of the row kernel's sources; a recorded ncu figure is used only
+    while it matches."""
     h = hashlib.sha256()
-    for f in ["qp_kernels.cu", "qp_internal.h"]:
+    for f in ["qp_sweep_rows.cu", "qp_device.cuh", "qp_internal.h"]:
         h.update(open(os.path.join(ROOT, "paper_2608_25376_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -88,7 +90,7 @@ def kernel_source_hash():
 def recorded_traffic(kernel_tag):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
     the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "sweep_structured_10x10.md")
+    p = os.path.join(ROOT, "profiles", "sweep_rows_10x10.md")
     if not os.path.exists(p):
         return None
     txt = open(p).read()
@@ -293,7 +295,7 @@ def run_ours(args):
     peak_tops = SMS * INT_LANES_PER_SM * sm_mhz * 1e6 / 1e12
     ann_ms = statistics.mean(anneal_ms)
     achieved_tops = OPS_PER_ATTEMPT * attempts / (ann_ms / 1e3) / 1e12
-    traffic = recorded_traffic("structured")
+    traffic = recorded_traffic("rows")
     roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
                 "frac": achieved_tops / peak_tops, "traffic": traffic,
                 "kernel": "k_sweep_rows" if args.structured_kernel == "rows" else "k_sweep_structured",
