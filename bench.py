@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-dense", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--replicas-per-cta", type=int, default=0)
     ap.add_argument("--structured-kernel", default="rows", choices=["rows", "flat"])
     ap.add_argument("--profile-case", default=None, choices=["rows", "flat", "dense"],
@@ -208,6 +209,43 @@ def run_reference(args):
     return 0
 
 
+def bench_batch(args, flush, stream):
+    """The batched workload: 256 fields (sides 4..16, 0-20% obstacles, irregular
+    boundaries, seed 2026) x 128 replicas x 2000 sweeps in one CUDA-graph launch,
+    configuration from the autotuner."""
+    import torch
+    from paper_2608_25376_gb300 import autotune, inputs, qpath
+    fields = inputs.batch(256, seed=2026)
+    hs = [qpath.qp_build_qubo(f) for f in fields]
+    R, S = 128, 2000
+    w, ctas = autotune.tune_batch(hs, R, S)
+    st = [torch.zeros((R, h.info["n"]), dtype=torch.uint8, device="cuda") for h in hs]
+    E = [torch.zeros(R, dtype=torch.int64, device="cuda") for _ in hs]
+    B = [torch.zeros(R, dtype=torch.int64, device="cuda") for _ in hs]
+    b = qpath.qp_batch_create(hs, R, qpath.schedule(S), 1, st, E, B, replicas_per_cta=w, ctas=ctas)
+    attempts = sum(R * S * (h.info["C"] - 1) ** 2 for h in hs)
+    with torch.cuda.stream(stream):
+        b.run(stream)
+        ms = []
+        for k in range(2):
+            flush.fill_(k)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.run(stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    m = statistics.mean(ms)
+    feas = sum(int((x < qpath.E_NONE).sum().item()) for x in B)
+    info = b.info
+    b.close()
+    Cs = [h.info["C"] for h in hs]
+    return {"value": attempts / (m / 1e3), "unit": UNIT, "ms": m, "fields": len(hs), "replicas": R, "sweeps": S,
+            "cells_min_median_max": [min(Cs), sorted(Cs)[len(Cs) // 2], max(Cs)], "attempts": attempts,
+            "replicas_per_cta": info["replicas_per_cta"], "ctas": info["ctas"], "launch": "one CUDA graph",
+            "feasible_replicas": feas}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -337,6 +375,9 @@ def run_ours(args):
                                       "column_bytes_per_launch": col_bytes,
                                       "column_GBps": col_bytes / (dm / 1e3) / 1e9,
                                       "hbm_peak_GBps": pk.get("hbm_gbs"), "peak_kind": pk_kind}}
+
+    if not args.no_batch and rank == 0:
+        line.setdefault("variants", {})["batched"] = bench_batch(args, flush, stream)
 
     if not args.no_e2e:
         pin_states = torch.empty((R, n), dtype=torch.uint8, pin_memory=True)

@@ -177,6 +177,39 @@ qp_status qp_anneal_noalloc(qp_handle *h, int32_t replicas, const qp_schedule *s
                             const uint8_t *init_states, uint8_t *states_out, int64_t *energies_out,
                             int64_t *best_out, int32_t replica_offset, void *cuda_stream);
 
+/* Many fields of uneven size annealed in one persistent launch (the same
+ * sampler as qp_anneal, batched over problems).  Field f runs `replicas`
+ * chains with replica indices 0..replicas-1 and seed + f, so its results equal
+ * qp_anneal(hs[f], replicas, sched, seed + f, NULL, ...) bit for bit.  Every
+ * handle must come from qp_build_qubo with int16 distances (QP_ERANGE
+ * otherwise; fields up to 512 cells); outputs are caller-owned device buffers
+ * (states_out[f]: replicas*C_f^2 bytes, energies_out[f] and best_out[f]:
+ * replicas int64; best_out or any best_out[f] may be NULL).
+ * qp_batch_create builds the field table and the work order (largest fields
+ * first), and captures a CUDA graph of {reset the work-queue head, launch the
+ * persistent kernel}; qp_batch_run replays it on a stream (asynchronous);
+ * qp_batch_destroy frees it.  The handles and output buffers must outlive the
+ * batch.  Taking work is one atomic add per (field, replica): no device wait.
+ * opts (NULL = defaults): replicas_per_cta (warps per CTA) and ctas (grid
+ * size, 0 = as many as fit on the GPU at once); the autotuner picks them. */
+typedef struct qp_batch qp_batch;
+typedef struct {
+  int32_t replicas_per_cta;
+  int32_t ctas;
+} qp_batch_opts;
+qp_status qp_batch_create(qp_handle *const *hs, int32_t count, int32_t replicas, const qp_schedule *sched,
+                          uint64_t seed, uint8_t *const *states_out, int64_t *const *energies_out,
+                          int64_t *const *best_out, const qp_batch_opts *opts, qp_batch **out);
+qp_status qp_batch_run(qp_batch *batch, void *cuda_stream);
+/* The configuration a batch was built with (any pointer may be NULL). */
+qp_status qp_batch_info(const qp_batch *batch, int32_t *replicas_per_cta, int32_t *ctas, int32_t *units);
+void qp_batch_destroy(qp_batch *batch);
+
+/* One-shot batch: create, run on cuda_stream, wait, destroy. */
+qp_status qp_anneal_batch(qp_handle *const *hs, int32_t count, int32_t replicas, const qp_schedule *sched,
+                          uint64_t seed, uint8_t *const *states_out, int64_t *const *energies_out,
+                          int64_t *const *best_out, void *cuda_stream);
+
 /* Algorithm 1 last step: the flight path of one state (n bytes, host or
  * device).  path_out[t] = cell id flown at step t (C int32, host), *length_out
  * = sum_t d(path[t], path[t+1]) (host).  QP_EINFEASIBLE if a row or column

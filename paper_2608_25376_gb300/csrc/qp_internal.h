@@ -81,6 +81,13 @@ bool structured_state_fits_smem(int C, bool d_i16, int warps_per_cta);
 bool rows_supported(int C, bool d_i16, int warps_per_cta);
 cudaError_t launch_rows(const StructArgs &a, bool d_i16, int warps_per_cta, cudaStream_t st,
                         LaunchInfo *info);
+// Batched persistent launch (qp_sweep_rows.cu): fields[] per field, units[]
+// = (field, replica) in processing order, counter = the work-queue head (zeroed
+// before each launch).  All fields must use int16 distances.
+bool batch_supported(int Cmax, int warps_per_cta);
+cudaError_t batch_prepare(int Cmax, int warps_per_cta, int *blocks_per_sm);
+cudaError_t launch_batch(const StructArgs *fields, const int2 *units, int n_units, int *counter, int Cmax,
+                         int warps_per_cta, int blocks, cudaStream_t st);
 cudaError_t launch_dense(const DenseArgs &a, bool s_i16, int warps_per_cta, cudaStream_t st,
                          LaunchInfo *info);
 bool dense_h_fits_smem(int64_t n, int C, int warps_per_cta);

@@ -203,41 +203,18 @@ __device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int
   return flipped;
 }
 
-// Widest rows (NCH = 4) keep three 16-register fields per lane: they get up to
-// 255 registers by capping the CTA at 8 replicas.
-template <int NCH>
-constexpr int rows_max_warps() { return NCH >= 4 ? 8 : kMaxWarpsPerCta; }
-
+// One replica of a field through the sweeps [sweep_begin, sweep_end): the
+// whole chain of the row kernel, shared by the single-field launch and the
+// batched persistent launch.  st: the replica's C x Cw row bitsets; hot1: its
+// per-row single-cell cache (C entries); d: the distance matrix (global or
+// shared memory, per DMODE).
 template <typename DT, int NCH, int DMODE>
-__global__ void __launch_bounds__(rows_max_warps<NCH>() * 32) k_sweep_rows(const StructArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+__device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_t *st, int16_t *hot1,
+                                             const void *d, int lane) {
   const int C = a.C, Cp = a.Cp, s0 = a.start, A = a.A, B = a.B;
   const int twoA = 2 * A;
   const int Cw = (C + 31) >> 5;
   const int n = C * C;
-  unsigned char *p = smem;
-  const void *d = a.d;
-  if (DMODE == 1) {
-    const int nv = (int)((size_t)C * Cp * sizeof(DT) / 16);
-    const int4 *src = static_cast<const int4 *>(a.d);
-    int4 *dst = reinterpret_cast<int4 *>(p);
-    for (int v = threadIdx.x; v < nv; v += blockDim.x) dst[v] = __ldg(src + v);
-    d = p;
-    p += align16r((size_t)C * Cp * sizeof(DT));
-  } else if (DMODE == 2) {
-    const DT *src = static_cast<const DT *>(a.d);
-    int *dst = reinterpret_cast<int *>(p);
-    for (int e = threadIdx.x; e < C * Cp; e += blockDim.x) dst[e] = (int)__ldg(src + e);
-    d = p;
-    p += align16r((size_t)C * Cp * 4);
-  }
-  const size_t per_warp = 4 * (size_t)a.nw_pad + align16r(2 * (size_t)C);
-  uint32_t *st = reinterpret_cast<uint32_t *>(p + warp * per_warp);
-  int16_t *hot1 = reinterpret_cast<int16_t *>(p + warp * per_warp + 4 * (size_t)a.nw_pad);
-  __syncthreads();
-  const int r = blockIdx.x * W + warp;
-  if (r >= a.R) return;  // no CTA-wide barrier after this point
   const uint32_t rg = (uint32_t)(a.rep_offset + r);
 
   // ---- initial state: given or all zero; row 0 and column s clamped (x_{0,s} = 1)
@@ -429,6 +406,69 @@ __global__ void __launch_bounds__(rows_max_warps<NCH>() * 32) k_sweep_rows(const
   }
 }
 
+
+// Widest rows (NCH = 4) keep three 16-register fields per lane: they get up to
+// 255 registers by capping the CTA at 8 replicas.
+template <int NCH>
+constexpr int rows_max_warps() { return NCH >= 4 ? 8 : kMaxWarpsPerCta; }
+
+template <typename DT, int NCH, int DMODE>
+__global__ void __launch_bounds__(rows_max_warps<NCH>() * 32) k_sweep_rows(const StructArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const int C = a.C, Cp = a.Cp;
+  unsigned char *p = smem;
+  const void *d = a.d;
+  if (DMODE == 1) {
+    const int nv = (int)((size_t)C * Cp * sizeof(DT) / 16);
+    const int4 *src = static_cast<const int4 *>(a.d);
+    int4 *dst = reinterpret_cast<int4 *>(p);
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) dst[v] = __ldg(src + v);
+    d = p;
+    p += align16r((size_t)C * Cp * sizeof(DT));
+  } else if (DMODE == 2) {
+    const DT *src = static_cast<const DT *>(a.d);
+    int *dst = reinterpret_cast<int *>(p);
+    for (int e = threadIdx.x; e < C * Cp; e += blockDim.x) dst[e] = (int)__ldg(src + e);
+    d = p;
+    p += align16r((size_t)C * Cp * 4);
+  }
+  const size_t per_warp = 4 * (size_t)a.nw_pad + align16r(2 * (size_t)C);
+  uint32_t *st = reinterpret_cast<uint32_t *>(p + warp * per_warp);
+  int16_t *hot1 = reinterpret_cast<int16_t *>(p + warp * per_warp + 4 * (size_t)a.nw_pad);
+  __syncthreads();
+  const int r = blockIdx.x * W + warp;
+  if (r >= a.R) return;  // no CTA-wide barrier after this point
+  rows_replica<DT, NCH, DMODE>(a, r, st, hot1, d, lane);
+}
+
+// Batched persistent sweep: many fields of uneven size in one launch.  Each
+// warp takes (field, replica) units from a global counter until none are left
+// and runs the same chain as k_sweep_rows for that replica; units are ordered
+// largest field first so the tail is made of short units.  Taking a unit is
+// one atomicAdd: no warp ever waits on another.  The distance matrices are
+// read from L2 (all fields of a batch together are a few MB).
+template <int NCH>
+__global__ void __launch_bounds__(rows_max_warps<NCH>() * 32)
+    k_sweep_batch(const StructArgs *fields, const int2 *units, int n_units, int *counter, int nw_pad_max,
+                  int Cmax) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const size_t per_warp = 4 * (size_t)nw_pad_max + align16r(2 * (size_t)Cmax);
+  uint32_t *st = reinterpret_cast<uint32_t *>(smem + warp * per_warp);
+  int16_t *hot1 = reinterpret_cast<int16_t *>(smem + warp * per_warp + 4 * (size_t)nw_pad_max);
+  while (true) {
+    int u = 0;
+    if (lane == 0) u = atomicAdd(counter, 1);
+    u = __shfl_sync(kFull, u, 0);
+    if (u >= n_units) break;
+    const int2 unit = units[u];
+    const StructArgs a = fields[unit.x];
+    rows_replica<int16_t, NCH, 0>(a, unit.y, st, hot1, a.d, lane);
+    __syncwarp();
+  }
+}
+
 constexpr size_t kSmemLimitRows = 227 * 1024;
 
 template <typename DT, int NCH, int DMODE>
@@ -467,6 +507,42 @@ size_t rows_smem(int C, bool d_i16, int W, int dmode) {
 bool rows_supported(int C, bool d_i16, int W) {
   const int wmax = C <= 256 ? kMaxWarpsPerCta : 8;
   return C <= 512 && W >= 1 && W <= wmax && rows_smem(C, d_i16, W, 0) <= kSmemLimitRows;
+}
+
+size_t batch_smem(int Cmax, int W) {
+  return (size_t)W * (4 * rows_state_words(Cmax) + align16r(2 * (size_t)Cmax));
+}
+
+bool batch_supported(int Cmax, int W) {
+  const int wmax = Cmax <= 256 ? kMaxWarpsPerCta : 8;
+  return Cmax >= 2 && Cmax <= 512 && W >= 1 && W <= wmax && batch_smem(Cmax, W) <= kSmemLimitRows;
+}
+
+template <int NCH>
+static cudaError_t prep_batch(int W, size_t smem, int *blocks_per_sm) {
+  auto k = k_sweep_batch<NCH>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, W * 32, smem);
+}
+
+cudaError_t batch_prepare(int Cmax, int W, int *blocks_per_sm) {
+  if (!batch_supported(Cmax, W)) return cudaErrorInvalidValue;
+  const size_t smem = batch_smem(Cmax, W);
+  if (Cmax <= 128) return prep_batch<1>(W, smem, blocks_per_sm);
+  if (Cmax <= 256) return prep_batch<2>(W, smem, blocks_per_sm);
+  return prep_batch<4>(W, smem, blocks_per_sm);
+}
+
+cudaError_t launch_batch(const StructArgs *fields, const int2 *units, int n_units, int *counter, int Cmax,
+                         int W, int blocks, cudaStream_t st) {
+  if (!batch_supported(Cmax, W) || blocks < 1) return cudaErrorInvalidValue;
+  const size_t smem = batch_smem(Cmax, W);
+  const int nwp = (int)rows_state_words(Cmax);
+  if (Cmax <= 128) k_sweep_batch<1><<<blocks, W * 32, smem, st>>>(fields, units, n_units, counter, nwp, Cmax);
+  else if (Cmax <= 256) k_sweep_batch<2><<<blocks, W * 32, smem, st>>>(fields, units, n_units, counter, nwp, Cmax);
+  else k_sweep_batch<4><<<blocks, W * 32, smem, st>>>(fields, units, n_units, counter, nwp, Cmax);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_rows(const StructArgs &a_in, bool d_i16, int W, cudaStream_t st, LaunchInfo *info) {

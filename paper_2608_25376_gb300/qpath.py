@@ -25,7 +25,8 @@ E_NONE = np.iinfo(np.int64).max
 
 # every entry point include/qpath.h declares
 SYMBOLS = ["qp_build_qubo", "qp_build_from_dense", "qp_qubo_info", "qp_export_dense", "qp_export_dist",
-           "qp_thresholds", "qp_anneal", "qp_anneal_ex", "qp_anneal_noalloc", "qp_decode_path",
+           "qp_thresholds", "qp_anneal", "qp_anneal_ex", "qp_anneal_noalloc", "qp_batch_create",
+           "qp_batch_run", "qp_batch_info", "qp_batch_destroy", "qp_anneal_batch", "qp_decode_path",
            "qp_decode_batch", "qp_destroy", "qp_last_error"]
 
 
@@ -42,6 +43,10 @@ class qp_field(ct.Structure):
 class qp_schedule(ct.Structure):
     _fields_ = [("n_sweeps", ct.c_int32), ("T0", ct.c_double), ("T1", ct.c_double),
                 ("sweep_begin", ct.c_int32), ("sweep_end", ct.c_int32)]
+
+
+class qp_batch_opts(ct.Structure):
+    _fields_ = [("replicas_per_cta", ct.c_int32), ("ctas", ct.c_int32)]
 
 
 class qp_anneal_opts(ct.Structure):
@@ -74,6 +79,11 @@ def lib():
                 "qp_anneal": [vp, i32, P(qp_schedule), u64, vp, vp, vp, vp, vp],
                 "qp_anneal_ex": [vp, i32, P(qp_schedule), u64, vp, vp, vp, vp, P(qp_anneal_opts), vp],
                 "qp_anneal_noalloc": [vp, i32, P(qp_schedule), u64, vp, vp, vp, vp, i32, vp],
+                "qp_batch_create": [P(vp), i32, i32, P(qp_schedule), u64, P(vp), P(vp), P(vp),
+                                    P(qp_batch_opts), P(vp)],
+                "qp_batch_run": [vp, vp],
+                "qp_batch_info": [vp, P(i32), P(i32), P(i32)],
+                "qp_anneal_batch": [P(vp), i32, i32, P(qp_schedule), u64, P(vp), P(vp), P(vp), vp],
                 "qp_decode_path": [vp, vp, vp, vp],
                 "qp_decode_batch": [vp, i32, vp, vp, vp, vp],
             }
@@ -81,6 +91,8 @@ def lib():
                 fn = getattr(L, name)
                 fn.argtypes = args
                 fn.restype = ct.c_int
+            L.qp_batch_destroy.argtypes = [vp]
+            L.qp_batch_destroy.restype = None
             L.qp_destroy.argtypes = [vp]
             L.qp_destroy.restype = None
             L.qp_last_error.argtypes = []
@@ -215,6 +227,74 @@ def qp_anneal_noalloc(h: Handle, replicas, sched, seed, init_states, states_out,
     _check(lib().qp_anneal_noalloc(h.ptr, int(replicas), ct.byref(sched), ct.c_uint64(seed), _ptr(init_states),
                                    _ptr(states_out), _ptr(energies_out), _ptr(best_out), int(replica_offset),
                                    _stream(stream)))
+
+
+def _ptr_array(xs):
+    arr = (ct.c_void_p * len(xs))()
+    for i, x in enumerate(xs):
+        p = _ptr(x)
+        arr[i] = None if p is None else p.value
+    return arr
+
+
+class Batch:
+    """Owns a qp_batch* (a captured CUDA graph over many fields)."""
+
+    def __init__(self, ptr, keep):
+        self.ptr = ptr
+        self._keep = keep  # handles and buffers must outlive the batch
+
+    def run(self, stream=None):
+        qp_batch_run(self, stream)
+
+    @property
+    def info(self):
+        return qp_batch_info(self)
+
+    def close(self):
+        if self.ptr:
+            lib().qp_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def qp_batch_create(handles, replicas, sched, seed, states_out, energies_out, best_out=None,
+                    replicas_per_cta=0, ctas=0) -> Batch:
+    hs = (ct.c_void_p * len(handles))(*[h.ptr.value for h in handles])
+    so, eo = _ptr_array(states_out), _ptr_array(energies_out)
+    bo = None if best_out is None else _ptr_array(best_out)
+    o = qp_batch_opts(int(replicas_per_cta), int(ctas))
+    out = ct.c_void_p()
+    _check(lib().qp_batch_create(hs, len(handles), int(replicas), ct.byref(sched), ct.c_uint64(seed), so, eo,
+                                 bo, ct.byref(o), ct.byref(out)))
+    return Batch(out, (handles, states_out, energies_out, best_out))
+
+
+def qp_batch_run(b: Batch, stream=None):
+    _check(lib().qp_batch_run(b.ptr, _stream(stream)))
+
+
+def qp_batch_info(b: Batch) -> dict:
+    w, c, u = ct.c_int32(), ct.c_int32(), ct.c_int32()
+    _check(lib().qp_batch_info(b.ptr, ct.byref(w), ct.byref(c), ct.byref(u)))
+    return dict(replicas_per_cta=w.value, ctas=c.value, units=u.value)
+
+
+def qp_batch_destroy(b: Batch):
+    b.close()
+
+
+def qp_anneal_batch(handles, replicas, sched, seed, states_out, energies_out, best_out=None, stream=None):
+    hs = (ct.c_void_p * len(handles))(*[h.ptr.value for h in handles])
+    so, eo = _ptr_array(states_out), _ptr_array(energies_out)
+    bo = None if best_out is None else _ptr_array(best_out)
+    _check(lib().qp_anneal_batch(hs, len(handles), int(replicas), ct.byref(sched), ct.c_uint64(seed), so, eo, bo,
+                                 _stream(stream)))
 
 
 def qp_decode_path(h: Handle, state):
