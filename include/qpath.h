@@ -222,6 +222,55 @@ qp_status qp_decode_path(const qp_handle *h, const uint8_t *state, int32_t *path
 qp_status qp_decode_batch(const qp_handle *h, int32_t replicas, const uint8_t *states,
                           int32_t *paths_out, int64_t *lengths_out, void *cuda_stream);
 
+/* ---- Learned warm start (no counterpart in the paper: a seed generator for
+ * the sampler).  A per-cell MLP maps 16 features of a free cell to logits over
+ * its step t in the flight path (t < 256): Linear(16,256)+ReLU,
+ * Linear(256,256)+ReLU x 2, Linear(256,256).  bf16 weights and activations,
+ * fp32 accumulation on the tensor cores (tcgen05), fp32 master weights and
+ * Adam moments.  Trained with softmax cross-entropy over the steps t < C of
+ * the cell's field, on paths the annealer itself found. */
+typedef struct qp_ws qp_ws;
+
+/* A model with He-uniform weights drawn from `seed` (zero biases). */
+qp_status qp_ws_create(uint64_t seed, qp_ws **out);
+void qp_ws_destroy(qp_ws *ws);
+/* Number of parameters; the flat layout of get/set is W1[256][16], b1[256],
+ * W2[256][256], b2, W3[256][256], b3, W4[256][256], b4 (fp32). */
+int64_t qp_ws_param_count(void);
+qp_status qp_ws_get_params(qp_ws *ws, float *params_out);
+qp_status qp_ws_set_params(qp_ws *ws, const float *params);
+
+/* The 16 features of every free cell of a field, in cell-id order (row-major
+ * free cells): x/15, y/15, blocked fraction of the 8 neighbours (obstacles or
+ * outside), start x/15, start y/15, W/16, H/16, C/256, (x-start x)/15,
+ * (y-start y)/15, x/(W-1), y/(H-1), free fraction of the 5x5 block, y mod 2,
+ * 1, 0.  feats_out: C*16 floats (host) or NULL to get only *n_cells. */
+qp_status qp_ws_features(const qp_field *field, float *feats_out, int32_t *n_cells);
+
+/* Logits for M cells: feats (M*16 fp32, host), logits_out (M*256 fp32, host or
+ * device).  QP_ETIMEOUT if a tensor-core wait gave up. */
+qp_status qp_ws_forward(qp_ws *ws, const float *feats, int32_t M, float *logits_out, void *cuda_stream);
+
+/* Gradients of the mean cross-entropy over M cells without updating: labels
+ * (M int32: the cell's step, -1 = ignore), steps (M int32: the cell's field
+ * size C, logits t >= C are masked).  grads_out (param_count floats, host, may
+ * be NULL) in the get/set layout; *loss_out = mean loss (may be NULL). */
+qp_status qp_ws_grads(qp_ws *ws, const float *feats, const int32_t *labels, const int32_t *steps, int32_t M,
+                      float *grads_out, float *loss_out, void *cuda_stream);
+
+/* One training step: gradients as in qp_ws_grads, then Adam (beta1 0.9,
+ * beta2 0.999, eps 1e-8) with learning rate lr. */
+qp_status qp_ws_train_step(qp_ws *ws, const float *feats, const int32_t *labels, const int32_t *steps, int32_t M,
+                           float lr, float *loss_out, void *cuda_stream);
+
+/* Logits of one field's C cells (row stride ld >= C, host) -> a feasible
+ * one-hot state (C*C bytes, t-major) and its path: the start cell takes step
+ * 0, then the largest remaining logit over unassigned cells and free steps
+ * fixes one (cell, step) pair at a time (ties: smaller cell, then smaller
+ * step).  Either output may be NULL. */
+qp_status qp_ws_decode(const float *logits, int32_t ld, int32_t C, int32_t start_cell, uint8_t *state_out,
+                       int32_t *path_out);
+
 /* Free a handle and its device memory (NULL is ignored). */
 void qp_destroy(qp_handle *h);
 

@@ -1,0 +1,385 @@
+// Kernels of the learned warm start: a per-cell bf16 MLP (features -> 3 x
+// Linear(256)+ReLU -> Linear(256) step logits), trained with softmax
+// cross-entropy on the annealer's own best paths.
+//
+// Every matrix product (forward, dX = dY W, dW = dY^T X) runs on one tcgen05
+// kernel: D[M x N] (+)= A[M x K] B[N x K]^T with bf16 operands (both K-major,
+// i.e. K contiguous) and fp32 accumulation in tensor memory.  A CTA owns a
+// 128 x N tile (N <= 256, multiple of 16) and walks K in chunks of 64: its
+// threads copy the two operand chunks into shared memory in the canonical
+// no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix, core
+// matrices adjacent along K 128 B apart, 8-row groups 1024 B apart), one
+// elected thread issues the 128 x N x 16 MMAs and commits them to an mbarrier,
+// and everybody waits on it (bounded) before the chunk buffer is refilled.
+// The epilogue reads the accumulator back with tcgen05.ld (warp w owns TMEM
+// lanes 32w..32w+31 = rows of the tile) and applies bias/ReLU/masking.
+// Split-K partial tiles are added into an fp32 output with atomics.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "qp_mlp.h"
+
+namespace qp {
+namespace mlp {
+namespace {
+
+constexpr int kTileM = 128;
+constexpr int kChunkK = 64;
+constexpr int kTmemCols = 256;
+constexpr size_t kSmemA = kTileM * kChunkK * 2;  // 16 KB
+constexpr size_t kSmemB = 256 * kChunkK * 2;     // 32 KB
+// 100 KB of dynamic shared memory keeps at most two CTAs (2 x 256 TMEM
+// columns = all 512) on an SM, so tcgen05.alloc never has to wait long.
+constexpr size_t kGemmSmem = 100 * 1024;
+constexpr long long kWaitCycles = 1000000000LL;  // ~0.5 s at 2 GHz, then give up
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address >> 4 in bits 0-13,
+// leading-dimension byte offset >> 4 in 16-29, stride-dimension byte offset
+// >> 4 in 32-45, descriptor version 1 in 46-47, no swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: fp32 D (bits 4-5 = 1), bf16 A and B
+// (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in
+// bits 17-22, M >> 4 in bits 24-28.
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of an mbarrier, giving up after kWaitCycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_test(mbar, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void proxy_fence() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// 16 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// rows [row0, row0 + nrows) x columns [k0, k0 + 64) of a row-major bf16 matrix
+// into the core-matrix layout; columns at or beyond kend (and rows beyond
+// nvalid) read as zero.  K offsets are multiples of 8 elements (16 B).
+__device__ __forceinline__ void stage_chunk(uint8_t *dst, const __nv_bfloat16 *src, int ld, int row0, int nrows,
+                                            int nvalid, int k0, int kend, int tid, int nthreads) {
+  for (int idx = tid; idx < nrows * 8; idx += nthreads) {
+    const int r = idx >> 3, seg = idx & 7;
+    const int m = row0 + r, k = k0 + seg * 8;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (m < nvalid && k < kend) v = __ldg(reinterpret_cast<const uint4 *>(src + (size_t)m * ld + k));
+    *reinterpret_cast<uint4 *>(dst + ((r >> 3) * 8 + seg) * 128 + (r & 7) * 16) = v;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail_flag;
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + kSmemA;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * kTileM;
+  const int N = g.N;
+  const int kbeg = blockIdx.z * g.k_per_split;
+  const int kend = min(g.K, kbeg + g.k_per_split);
+
+  if (warp == 0) tmem_alloc(smem_u32(&tmem_slot), kTmemCols);
+  if (tid == 0) {
+    mbar_init(smem_u32(&mbar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fail_flag = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = idesc_bf16(kTileM, N);
+  uint32_t parity = 0;
+  int issued = 0;
+  for (int k0 = kbeg; k0 < kend; k0 += kChunkK) {
+    stage_chunk(sA, g.A, g.lda, m0, kTileM, g.M, k0, kend, tid, 128);
+    stage_chunk(sB, g.B, g.ldb, 0, N, N, k0, kend, tid, 128);
+    proxy_fence();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const int ksteps = min(4, (kend - k0 + 15) / 16);
+      for (int kk = 0; kk < ksteps; ++kk) {
+        const uint64_t ad = smem_desc(smem_u32(sA) + kk * 256, 128, 1024);
+        const uint64_t bd = smem_desc(smem_u32(sB) + kk * 256, 128, 1024);
+        mma_bf16(tmem, ad, bd, idesc, (issued > 0 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(smem_u32(&mbar));
+    }
+    ++issued;
+    const bool ok = mbar_wait(smem_u32(&mbar), parity);
+    parity ^= 1u;
+    if (!ok) fail_flag = 1;
+    __syncthreads();
+    if (fail_flag) break;
+  }
+  tc_fence_after();
+  if (!fail_flag && issued > 0) {
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      float v[16];
+      tmem_ld16(lane_base + c0, v);
+      if (row >= g.M) continue;
+      if (g.mode == kEpiBiasRelu || g.mode == kEpiBiasF32) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] += g.bias ? g.bias[c0 + i] : 0.0f;
+      }
+      if (g.mode == kEpiBiasRelu) {
+        __nv_bfloat16 *o = g.out_bf16 + (size_t)row * g.ldo + c0;
+#pragma unroll
+        for (int i = 0; i < 16; i += 2)
+          *reinterpret_cast<__nv_bfloat162 *>(o + i) = __floats2bfloat162_rn(fmaxf(v[i], 0.0f), fmaxf(v[i + 1], 0.0f));
+      } else if (g.mode == kEpiBiasF32) {
+        float *o = g.out_f32 + (size_t)row * g.ldo + c0;
+#pragma unroll
+        for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4 *>(o + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+      } else if (g.mode == kEpiAtomicF32) {
+        float *o = g.out_f32 + (size_t)row * g.ldo + c0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) atomicAdd(o + i, v[i]);
+      } else {  // kEpiReluMask: gradient through the ReLU of a stored activation
+        const __nv_bfloat16 *ref = g.relu_ref + (size_t)row * g.ldr + c0;
+        __nv_bfloat16 *o = g.out_bf16 + (size_t)row * g.ldo + c0;
+#pragma unroll
+        for (int i = 0; i < 16; i += 2) {
+          const float a = __bfloat162float(ref[i]) > 0.0f ? v[i] : 0.0f;
+          const float b = __bfloat162float(ref[i + 1]) > 0.0f ? v[i + 1] : 0.0f;
+          *reinterpret_cast<__nv_bfloat162 *>(o + i) = __floats2bfloat162_rn(a, b);
+        }
+      }
+    }
+  }
+  if (fail_flag && tid == 0 && g.err) atomicExch(g.err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// Softmax cross-entropy over the valid steps t < steps[m] of each cell row;
+// rows with label < 0 are padding.  dZ = (softmax - onehot) * inv_rows (bf16),
+// loss_sum += -log p[label].  One warp per row, 8 columns per lane.
+__global__ void k_softmax_ce(const float *Z, int ldz, const int32_t *label, const int32_t *steps, int M,
+                             float inv_rows, __nv_bfloat16 *dZ, int ldd, float *loss_sum) {
+  const int lane = threadIdx.x & 31;
+  const int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (m >= M) return;
+  const int y = label[m], T = steps[m];
+  float v[8];
+  float mx = -INFINITY;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int t = lane * 8 + i;
+    v[i] = (y >= 0 && t < T) ? Z[(size_t)m * ldz + t] : -INFINITY;
+    mx = fmaxf(mx, v[i]);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  float s = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    v[i] = (y >= 0 && lane * 8 + i < T) ? expf(v[i] - mx) : 0.0f;
+    s += v[i];
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __nv_bfloat16 *d = dZ + (size_t)m * ldd;
+#pragma unroll
+  for (int i = 0; i < 8; i += 2) {
+    const int t = lane * 8 + i;
+    float g0 = 0.0f, g1 = 0.0f;
+    if (y >= 0) {
+      g0 = (v[i] / s - (t == y ? 1.0f : 0.0f)) * inv_rows;
+      g1 = (v[i + 1] / s - (t + 1 == y ? 1.0f : 0.0f)) * inv_rows;
+    }
+    *reinterpret_cast<__nv_bfloat162 *>(d + t) = __floats2bfloat162_rn(g0, g1);
+  }
+  if (y >= 0 && lane == (y >> 3)) {
+    const float py = v[y & 7] / s;
+    atomicAdd(loss_sum, -logf(fmaxf(py, 1e-30f)));
+  }
+}
+
+// db[n] += sum_m dY[m][n] over a slab of rows (fp32 atomics).
+__global__ void k_colsum(const __nv_bfloat16 *Y, int ld, int M, int N, float *out) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int rows_per = (M + gridDim.y - 1) / gridDim.y;
+  const int r0 = blockIdx.y * rows_per, r1 = min(M, r0 + rows_per);
+  float s = 0.0f;
+  for (int m = r0; m < r1; ++m) s += __bfloat162float(Y[(size_t)m * ld + n]);
+  atomicAdd(out + n, s);
+}
+
+// out[c][r] = in[r][c] for a bf16 R x C matrix (32 x 32 tiles).
+__global__ void k_transpose(const __nv_bfloat16 *in, int R, int Cc, int ldi, __nv_bfloat16 *out, int ldo) {
+  __shared__ __nv_bfloat16 tile[32][33];
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int r = blockIdx.y * 32 + j;
+    tile[j][threadIdx.x] = (r < R && c < Cc) ? in[(size_t)r * ldi + c] : __float2bfloat16(0.0f);
+  }
+  __syncthreads();
+  const int r2 = blockIdx.y * 32 + threadIdx.x;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int c2 = blockIdx.x * 32 + j;
+    if (c2 < Cc && r2 < R) out[(size_t)c2 * ldo + r2] = tile[threadIdx.x][j];
+  }
+}
+
+// Adam on an fp32 master copy; writes the bf16 weight (rows x cols, row-major)
+// and, when wt != null, its transpose.
+__global__ void k_adam(float *w, float *m, float *v, const float *g, int rows, int cols, float lr, float b1,
+                       float b2, float eps, float c1, float c2, __nv_bfloat16 *wb, __nv_bfloat16 *wt) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  const float gr = g[e];
+  const float mm = b1 * m[e] + (1.0f - b1) * gr;
+  const float vv = b2 * v[e] + (1.0f - b2) * gr * gr;
+  m[e] = mm;
+  v[e] = vv;
+  const float upd = lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+  const float nw = w[e] - upd;
+  w[e] = nw;
+  if (wb) {
+    const __nv_bfloat16 b = __float2bfloat16(nw);
+    wb[e] = b;
+    if (wt) wt[(size_t)(e % cols) * rows + e / cols] = b;
+  }
+}
+
+__global__ void k_f32_to_bf16(const float *in, __nv_bfloat16 *out, int n) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = __float2bfloat16(in[e]);
+}
+
+}  // namespace
+
+cudaError_t gemm(const GemmArgs &g, int splits, cudaStream_t st) {
+  if (g.N < 16 || g.N > 256 || (g.N & 15) || (g.K & 15) || (g.lda & 7) || (g.ldb & 7) || splits < 1)
+    return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  GemmArgs a = g;
+  int kps = (g.K + splits - 1) / splits;
+  kps = (kps + kChunkK - 1) / kChunkK * kChunkK;
+  a.k_per_split = kps;
+  const int zs = (g.K + kps - 1) / kps;
+  dim3 grid((g.M + kTileM - 1) / kTileM, 1, zs);
+  k_gemm_tc<<<grid, 128, kGemmSmem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t softmax_ce(const float *Z, int ldz, const int32_t *label, const int32_t *steps, int M, float inv_rows,
+                       __nv_bfloat16 *dZ, int ldd, float *loss_sum, cudaStream_t st) {
+  k_softmax_ce<<<(M + 7) / 8, 256, 0, st>>>(Z, ldz, label, steps, M, inv_rows, dZ, ldd, loss_sum);
+  return cudaGetLastError();
+}
+
+cudaError_t colsum(const __nv_bfloat16 *Y, int ld, int M, int N, float *out, cudaStream_t st) {
+  dim3 grid((N + 127) / 128, 64);
+  k_colsum<<<grid, 128, 0, st>>>(Y, ld, M, N, out);
+  return cudaGetLastError();
+}
+
+cudaError_t transpose(const __nv_bfloat16 *in, int R, int Cc, int ldi, __nv_bfloat16 *out, int ldo,
+                      cudaStream_t st) {
+  dim3 grid((Cc + 31) / 32, (R + 31) / 32), block(32, 8);
+  k_transpose<<<grid, block, 0, st>>>(in, R, Cc, ldi, out, ldo);
+  return cudaGetLastError();
+}
+
+cudaError_t adam(float *w, float *m, float *v, const float *g, int rows, int cols, float lr, float b1, float b2,
+                 float eps, int step, __nv_bfloat16 *wb, __nv_bfloat16 *wt, cudaStream_t st) {
+  const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+  const int n = rows * cols;
+  k_adam<<<(n + 255) / 256, 256, 0, st>>>(w, m, v, g, rows, cols, lr, b1, b2, eps, c1, c2, wb, wt);
+  return cudaGetLastError();
+}
+
+cudaError_t to_bf16(const float *in, __nv_bfloat16 *out, int n, cudaStream_t st) {
+  k_f32_to_bf16<<<(n + 255) / 256, 256, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace mlp
+}  // namespace qp

@@ -1,0 +1,47 @@
+// Internal interface of the warm-start MLP kernels (qp_mlp.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qp {
+namespace mlp {
+
+enum EpiMode {
+  kEpiBiasRelu = 0,   // out_bf16 = bf16(relu(acc + bias))
+  kEpiBiasF32 = 1,    // out_f32 = acc + bias
+  kEpiAtomicF32 = 2,  // out_f32 += acc (split-K weight gradients)
+  kEpiReluMask = 3,   // out_bf16 = bf16(relu_ref > 0 ? acc : 0)
+};
+
+// D[M x N] (+)= A[M x K] B[N x K]^T; A, B bf16 row-major with K contiguous.
+// N in [16, 256] and a multiple of 16; K, lda, ldb multiples of 16 / 8.
+struct GemmArgs {
+  const __nv_bfloat16 *A;
+  int lda;
+  const __nv_bfloat16 *B;
+  int ldb;
+  int M, N, K;
+  int k_per_split;  // set by gemm()
+  int mode;
+  const float *bias;
+  float *out_f32;
+  __nv_bfloat16 *out_bf16;
+  int ldo;
+  const __nv_bfloat16 *relu_ref;
+  int ldr;
+  int *err;  // set to 1 if a bounded wait gave up
+};
+
+cudaError_t gemm(const GemmArgs &g, int splits, cudaStream_t st);
+cudaError_t softmax_ce(const float *Z, int ldz, const int32_t *label, const int32_t *steps, int M, float inv_rows,
+                       __nv_bfloat16 *dZ, int ldd, float *loss_sum, cudaStream_t st);
+cudaError_t colsum(const __nv_bfloat16 *Y, int ld, int M, int N, float *out, cudaStream_t st);
+cudaError_t transpose(const __nv_bfloat16 *in, int R, int C, int ldi, __nv_bfloat16 *out, int ldo, cudaStream_t st);
+cudaError_t adam(float *w, float *m, float *v, const float *g, int rows, int cols, float lr, float b1, float b2,
+                 float eps, int step, __nv_bfloat16 *wb, __nv_bfloat16 *wt, cudaStream_t st);
+cudaError_t to_bf16(const float *in, __nv_bfloat16 *out, int n, cudaStream_t st);
+
+}  // namespace mlp
+}  // namespace qp

@@ -1,0 +1,486 @@
+// Host side of the learned warm start: per-cell features of a field, the MLP
+// (16 -> 256 -> 256 -> 256 -> 256 step logits, bf16 weights with fp32 masters
+// and Adam moments), its forward pass, one training step (forward, softmax
+// cross-entropy, backward, Adam) built from the tcgen05 GEMM and the small
+// kernels of qp_mlp.cu, and the greedy decode of step logits into a feasible
+// one-hot state.  The public contract is in include/qpath.h.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "qp_internal.h"
+#include "qp_mlp.h"
+
+using namespace qp;
+
+namespace {
+
+constexpr int kIn = 16, kHid = 256, kOut = 256;
+constexpr int kLayers = 4;
+const int kDimIn[kLayers] = {kIn, kHid, kHid, kHid};
+const int kDimOut[kLayers] = {kHid, kHid, kHid, kOut};
+
+struct Buf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  ~Buf() {
+    if (p) cudaFree(p);
+  }
+  bool ensure(size_t want) {
+    if (want <= bytes) return true;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return false;
+    }
+    bytes = want;
+    return true;
+  }
+  template <typename T>
+  T *as() const { return static_cast<T *>(p); }
+};
+
+#define WS_CU(call)                                                                   \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) return set_error(QP_ECUDA, cudaGetErrorString(e_));        \
+  } while (0)
+#define WS_ALLOC(buf, bytes)                                                          \
+  do {                                                                                \
+    if (!(buf).ensure(bytes)) return set_error(QP_ENOMEM, "warm start: cudaMalloc failed"); \
+  } while (0)
+
+uint16_t f32_to_bf16_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7F800000u) == 0x7F800000u) return (uint16_t)(u >> 16);  // inf / nan
+  u += 0x7FFFu + ((u >> 16) & 1u);                                     // round half to even
+  return (uint16_t)(u >> 16);
+}
+
+uint64_t splitmix64(uint64_t &s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+}  // namespace
+
+struct qp_ws {
+  int dev = 0;
+  int step = 0;
+  Buf w[kLayers], b[kLayers];          // fp32 masters
+  Buf mw[kLayers], vw[kLayers], mb[kLayers], vb[kLayers];
+  Buf gw[kLayers], gb[kLayers];        // fp32 gradients
+  Buf wb[kLayers], wt[kLayers];        // bf16 weight and its transpose
+  int cap = 0;                         // rows the activation buffers hold
+  Buf x0, h[3], z, dz, dh[3], t1, t2, lab, stp, loss, err;
+};
+
+namespace {
+
+size_t n_params() {
+  size_t n = 0;
+  for (int l = 0; l < kLayers; ++l) n += (size_t)kDimOut[l] * kDimIn[l] + kDimOut[l];
+  return n;
+}
+
+qp_status ensure_rows(qp_ws *m, int Mp) {
+  if (Mp <= m->cap) return QP_OK;
+  WS_ALLOC(m->x0, (size_t)Mp * kIn * 2);
+  for (int i = 0; i < 3; ++i) {
+    WS_ALLOC(m->h[i], (size_t)Mp * kHid * 2);
+    WS_ALLOC(m->dh[i], (size_t)Mp * kHid * 2);
+  }
+  WS_ALLOC(m->z, (size_t)Mp * kOut * 4);
+  WS_ALLOC(m->dz, (size_t)Mp * kOut * 2);
+  WS_ALLOC(m->t1, (size_t)Mp * kHid * 2);
+  WS_ALLOC(m->t2, (size_t)Mp * kHid * 2);
+  WS_ALLOC(m->lab, (size_t)Mp * 4);
+  WS_ALLOC(m->stp, (size_t)Mp * 4);
+  m->cap = Mp;
+  return QP_OK;
+}
+
+// bf16 copies of every weight (and transposes) from the fp32 masters
+qp_status refresh_bf16(qp_ws *m, cudaStream_t st) {
+  for (int l = 0; l < kLayers; ++l) {
+    const int rows = kDimOut[l], cols = kDimIn[l];
+    std::vector<float> wh((size_t)rows * cols);
+    WS_CU(cudaMemcpyAsync(wh.data(), m->w[l].p, wh.size() * 4, cudaMemcpyDeviceToHost, st));
+    WS_CU(cudaStreamSynchronize(st));
+    std::vector<uint16_t> a(wh.size()), t(wh.size());
+    for (int r = 0; r < rows; ++r)
+      for (int c = 0; c < cols; ++c) {
+        const uint16_t v = f32_to_bf16_bits(wh[(size_t)r * cols + c]);
+        a[(size_t)r * cols + c] = v;
+        t[(size_t)c * rows + r] = v;
+      }
+    WS_CU(cudaMemcpyAsync(m->wb[l].p, a.data(), a.size() * 2, cudaMemcpyHostToDevice, st));
+    WS_CU(cudaMemcpyAsync(m->wt[l].p, t.data(), t.size() * 2, cudaMemcpyHostToDevice, st));
+  }
+  WS_CU(cudaStreamSynchronize(st));
+  return QP_OK;
+}
+
+qp_status upload_inputs(qp_ws *m, const float *feats, int M, int Mp, const int32_t *labels, const int32_t *steps,
+                        cudaStream_t st) {
+  if (qp_status s = ensure_rows(m, Mp); s != QP_OK) return s;
+  std::vector<uint16_t> xb((size_t)Mp * kIn, 0);
+  for (size_t e = 0; e < (size_t)M * kIn; ++e) xb[e] = f32_to_bf16_bits(feats[e]);
+  WS_CU(cudaMemcpyAsync(m->x0.p, xb.data(), xb.size() * 2, cudaMemcpyHostToDevice, st));
+  if (labels && steps) {
+    std::vector<int32_t> lb(Mp, -1), sp(Mp, 1);
+    std::memcpy(lb.data(), labels, (size_t)M * 4);
+    std::memcpy(sp.data(), steps, (size_t)M * 4);
+    WS_CU(cudaMemcpyAsync(m->lab.p, lb.data(), (size_t)Mp * 4, cudaMemcpyHostToDevice, st));
+    WS_CU(cudaMemcpyAsync(m->stp.p, sp.data(), (size_t)Mp * 4, cudaMemcpyHostToDevice, st));
+    WS_CU(cudaStreamSynchronize(st));
+  } else {
+    WS_CU(cudaStreamSynchronize(st));
+  }
+  return QP_OK;
+}
+
+mlp::GemmArgs gargs(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M, int N, int K,
+                    int mode, int *err) {
+  mlp::GemmArgs g{};
+  g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.M = M; g.N = N; g.K = K; g.mode = mode; g.err = err;
+  return g;
+}
+
+qp_status forward(qp_ws *m, int Mp, cudaStream_t st) {
+  const __nv_bfloat16 *in = m->x0.as<__nv_bfloat16>();
+  int ldin = kIn;
+  for (int l = 0; l < kLayers; ++l) {
+    mlp::GemmArgs g = gargs(in, ldin, m->wb[l].as<__nv_bfloat16>(), kDimIn[l], Mp, kDimOut[l], kDimIn[l],
+                            l < 3 ? mlp::kEpiBiasRelu : mlp::kEpiBiasF32, m->err.as<int>());
+    g.bias = m->b[l].as<float>();
+    if (l < 3) {
+      g.out_bf16 = m->h[l].as<__nv_bfloat16>();
+      g.ldo = kHid;
+    } else {
+      g.out_f32 = m->z.as<float>();
+      g.ldo = kOut;
+    }
+    WS_CU(mlp::gemm(g, 1, st));
+    in = m->h[l < 3 ? l : 2].as<__nv_bfloat16>();
+    ldin = kHid;
+  }
+  return QP_OK;
+}
+
+// Gradients of the mean cross-entropy into gw/gb (fp32); loss sum into m->loss.
+qp_status backward(qp_ws *m, int M, int Mp, cudaStream_t st) {
+  WS_CU(cudaMemsetAsync(m->loss.p, 0, 4, st));
+  WS_CU(mlp::softmax_ce(m->z.as<float>(), kOut, m->lab.as<int32_t>(), m->stp.as<int32_t>(), Mp, 1.0f / (float)M,
+                        m->dz.as<__nv_bfloat16>(), kOut, m->loss.as<float>(), st));
+  const __nv_bfloat16 *dy = m->dz.as<__nv_bfloat16>();
+  const int splits = std::max(1, Mp / 512);
+  for (int l = kLayers - 1; l >= 0; --l) {
+    const int nout = kDimOut[l], nin = kDimIn[l];
+    const __nv_bfloat16 *x = l == 0 ? m->x0.as<__nv_bfloat16>() : m->h[l - 1].as<__nv_bfloat16>();
+    // dW[out][in] = sum_m dY[m][out] X[m][in]  (operands transposed so m is contiguous)
+    __nv_bfloat16 *dyt = m->t1.as<__nv_bfloat16>(), *xt = m->t2.as<__nv_bfloat16>();
+    WS_CU(mlp::transpose(dy, Mp, nout, nout, dyt, Mp, st));
+    WS_CU(mlp::transpose(x, Mp, nin, nin, xt, Mp, st));
+    WS_CU(cudaMemsetAsync(m->gw[l].p, 0, (size_t)nout * nin * 4, st));
+    WS_CU(cudaMemsetAsync(m->gb[l].p, 0, (size_t)nout * 4, st));
+    mlp::GemmArgs g = gargs(dyt, Mp, xt, Mp, nout, nin, Mp, mlp::kEpiAtomicF32, m->err.as<int>());
+    g.out_f32 = m->gw[l].as<float>();
+    g.ldo = nin;
+    WS_CU(mlp::gemm(g, splits, st));
+    WS_CU(mlp::colsum(dy, nout, Mp, nout, m->gb[l].as<float>(), st));
+    if (l == 0) break;
+    // dX[m][in] = relu'(X) * sum_out dY[m][out] W[out][in]  (B = W^T, out contiguous)
+    mlp::GemmArgs gx = gargs(dy, nout, m->wt[l].as<__nv_bfloat16>(), nout, Mp, nin, nout, mlp::kEpiReluMask,
+                             m->err.as<int>());
+    gx.out_bf16 = m->dh[l - 1].as<__nv_bfloat16>();
+    gx.ldo = nin;
+    gx.relu_ref = x;
+    gx.ldr = nin;
+    WS_CU(mlp::gemm(gx, 1, st));
+    dy = m->dh[l - 1].as<__nv_bfloat16>();
+  }
+  return QP_OK;
+}
+
+qp_status check_err(qp_ws *m, cudaStream_t st) {
+  int e = 0;
+  WS_CU(cudaMemcpyAsync(&e, m->err.p, 4, cudaMemcpyDeviceToHost, st));
+  WS_CU(cudaStreamSynchronize(st));
+  if (e) {
+    WS_CU(cudaMemsetAsync(m->err.p, 0, 4, st));
+    return set_error(QP_ETIMEOUT, "warm start: a tensor-core wait gave up");
+  }
+  return QP_OK;
+}
+
+struct DevGuard {
+  int prev = -1;
+  explicit DevGuard(int dev) {
+    int cur = 0;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != dev) {
+      prev = cur;
+      cudaSetDevice(dev);
+    }
+  }
+  ~DevGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+extern "C" qp_status qp_ws_create(uint64_t seed, qp_ws **out) {
+  if (!out) return set_error(QP_EINVAL, "out is NULL");
+  *out = nullptr;
+  qp_ws *m = new qp_ws();
+  if (cudaGetDevice(&m->dev) != cudaSuccess) {
+    delete m;
+    return set_error(QP_ECUDA, "cudaGetDevice failed");
+  }
+  uint64_t s = seed;
+  for (int l = 0; l < kLayers; ++l) {
+    const int rows = kDimOut[l], cols = kDimIn[l];
+    const size_t nw = (size_t)rows * cols;
+    bool ok = m->w[l].ensure(nw * 4) && m->b[l].ensure(rows * 4) && m->mw[l].ensure(nw * 4) &&
+              m->vw[l].ensure(nw * 4) && m->mb[l].ensure(rows * 4) && m->vb[l].ensure(rows * 4) &&
+              m->gw[l].ensure(nw * 4) && m->gb[l].ensure(rows * 4) && m->wb[l].ensure(nw * 2) &&
+              m->wt[l].ensure(nw * 2);
+    if (!ok) {
+      delete m;
+      return set_error(QP_ENOMEM, "warm start: cudaMalloc failed");
+    }
+    // He-uniform initialisation from a splitmix64 stream
+    const double lim = std::sqrt(6.0 / cols);
+    std::vector<float> wh(nw);
+    for (size_t e = 0; e < nw; ++e) {
+      const double u = (double)(splitmix64(s) >> 11) * (1.0 / 9007199254740992.0);
+      wh[e] = (float)((2.0 * u - 1.0) * lim);
+    }
+    cudaMemcpy(m->w[l].p, wh.data(), nw * 4, cudaMemcpyHostToDevice);
+    cudaMemset(m->b[l].p, 0, rows * 4);
+    cudaMemset(m->mw[l].p, 0, nw * 4);
+    cudaMemset(m->vw[l].p, 0, nw * 4);
+    cudaMemset(m->mb[l].p, 0, rows * 4);
+    cudaMemset(m->vb[l].p, 0, rows * 4);
+  }
+  if (!m->loss.ensure(4) || !m->err.ensure(4)) {
+    delete m;
+    return set_error(QP_ENOMEM, "warm start: cudaMalloc failed");
+  }
+  cudaMemset(m->err.p, 0, 4);
+  const qp_status st = refresh_bf16(m, nullptr);
+  if (st != QP_OK) {
+    delete m;
+    return st;
+  }
+  *out = m;
+  return QP_OK;
+}
+
+extern "C" void qp_ws_destroy(qp_ws *m) {
+  if (!m) return;
+  DevGuard g(m->dev);
+  delete m;
+}
+
+extern "C" int64_t qp_ws_param_count(void) { return (int64_t)n_params(); }
+
+extern "C" qp_status qp_ws_get_params(qp_ws *m, float *out) {
+  if (!m || !out) return set_error(QP_EINVAL, "NULL argument");
+  DevGuard g(m->dev);
+  size_t o = 0;
+  for (int l = 0; l < kLayers; ++l) {
+    const size_t nw = (size_t)kDimOut[l] * kDimIn[l];
+    WS_CU(cudaMemcpy(out + o, m->w[l].p, nw * 4, cudaMemcpyDeviceToHost));
+    o += nw;
+    WS_CU(cudaMemcpy(out + o, m->b[l].p, (size_t)kDimOut[l] * 4, cudaMemcpyDeviceToHost));
+    o += kDimOut[l];
+  }
+  return QP_OK;
+}
+
+extern "C" qp_status qp_ws_set_params(qp_ws *m, const float *in) {
+  if (!m || !in) return set_error(QP_EINVAL, "NULL argument");
+  DevGuard g(m->dev);
+  size_t o = 0;
+  for (int l = 0; l < kLayers; ++l) {
+    const size_t nw = (size_t)kDimOut[l] * kDimIn[l];
+    WS_CU(cudaMemcpy(m->w[l].p, in + o, nw * 4, cudaMemcpyHostToDevice));
+    o += nw;
+    WS_CU(cudaMemcpy(m->b[l].p, in + o, (size_t)kDimOut[l] * 4, cudaMemcpyHostToDevice));
+    o += kDimOut[l];
+  }
+  return refresh_bf16(m, nullptr);
+}
+
+extern "C" qp_status qp_ws_forward(qp_ws *m, const float *feats, int32_t M, float *logits_out, void *stream) {
+  if (!m || !feats || !logits_out || M < 1) return set_error(QP_EINVAL, "bad argument");
+  DevGuard g(m->dev);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int Mp = (M + 127) / 128 * 128;
+  if (qp_status s = upload_inputs(m, feats, M, Mp, nullptr, nullptr, st); s != QP_OK) return s;
+  if (qp_status s = forward(m, Mp, st); s != QP_OK) return s;
+  WS_CU(cudaMemcpyAsync(logits_out, m->z.p, (size_t)M * kOut * 4, cudaMemcpyDefault, st));
+  return check_err(m, st);
+}
+
+extern "C" qp_status qp_ws_grads(qp_ws *m, const float *feats, const int32_t *labels, const int32_t *steps,
+                                 int32_t M, float *grads_out, float *loss_out, void *stream) {
+  if (!m || !feats || !labels || !steps || M < 1) return set_error(QP_EINVAL, "bad argument");
+  DevGuard g(m->dev);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int Mp = (M + 127) / 128 * 128;
+  if (qp_status s = upload_inputs(m, feats, M, Mp, labels, steps, st); s != QP_OK) return s;
+  if (qp_status s = forward(m, Mp, st); s != QP_OK) return s;
+  if (qp_status s = backward(m, M, Mp, st); s != QP_OK) return s;
+  if (qp_status s = check_err(m, st); s != QP_OK) return s;
+  if (grads_out) {
+    size_t o = 0;
+    for (int l = 0; l < kLayers; ++l) {
+      const size_t nw = (size_t)kDimOut[l] * kDimIn[l];
+      WS_CU(cudaMemcpy(grads_out + o, m->gw[l].p, nw * 4, cudaMemcpyDeviceToHost));
+      o += nw;
+      WS_CU(cudaMemcpy(grads_out + o, m->gb[l].p, (size_t)kDimOut[l] * 4, cudaMemcpyDeviceToHost));
+      o += kDimOut[l];
+    }
+  }
+  if (loss_out) {
+    float ls = 0.0f;
+    WS_CU(cudaMemcpy(&ls, m->loss.p, 4, cudaMemcpyDeviceToHost));
+    *loss_out = ls / (float)M;
+  }
+  return QP_OK;
+}
+
+extern "C" qp_status qp_ws_train_step(qp_ws *m, const float *feats, const int32_t *labels, const int32_t *steps,
+                                      int32_t M, float lr, float *loss_out, void *stream) {
+  const qp_status s0 = qp_ws_grads(m, feats, labels, steps, M, nullptr, loss_out, stream);
+  if (s0 != QP_OK) return s0;
+  DevGuard g(m->dev);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  m->step += 1;
+  for (int l = 0; l < kLayers; ++l) {
+    const int rows = kDimOut[l], cols = kDimIn[l];
+    WS_CU(mlp::adam(m->w[l].as<float>(), m->mw[l].as<float>(), m->vw[l].as<float>(), m->gw[l].as<float>(), rows,
+                    cols, lr, 0.9f, 0.999f, 1e-8f, m->step, m->wb[l].as<__nv_bfloat16>(),
+                    m->wt[l].as<__nv_bfloat16>(), st));
+    WS_CU(mlp::adam(m->b[l].as<float>(), m->mb[l].as<float>(), m->vb[l].as<float>(), m->gb[l].as<float>(), 1,
+                    rows, lr, 0.9f, 0.999f, 1e-8f, m->step, nullptr, nullptr, st));
+  }
+  return QP_OK;
+}
+
+// ----------------------------------------------------------------------------- features
+extern "C" qp_status qp_ws_features(const qp_field *f, float *feats_out, int32_t *n_cells) {
+  if (!f || f->rows < 1 || f->cols < 1) return set_error(QP_EINVAL, "bad field");
+  const int H = f->rows, W = f->cols;
+  auto isfree = [&](int r, int c) {
+    if (r < 0 || r >= H || c < 0 || c >= W) return false;
+    return !f->free_mask || f->free_mask[r * W + c] != 0;
+  };
+  if (f->start < 0 || f->start >= H * W || !isfree(f->start / W, f->start % W))
+    return set_error(QP_EINVAL, "start cell is not a free cell of the grid");
+  const int rs = f->start / W, cs = f->start % W;
+  int C = 0;
+  for (int r = 0; r < H; ++r)
+    for (int c = 0; c < W; ++c) C += isfree(r, c);
+  if (n_cells) *n_cells = C;
+  if (!feats_out) return QP_OK;
+  int k = 0;
+  for (int r = 0; r < H; ++r)
+    for (int c = 0; c < W; ++c) {
+      if (!isfree(r, c)) continue;
+      int blocked8 = 0, free25 = 0;
+      for (int dr = -2; dr <= 2; ++dr)
+        for (int dc = -2; dc <= 2; ++dc) {
+          const bool fr = isfree(r + dr, c + dc);
+          free25 += fr;
+          if (std::abs(dr) <= 1 && std::abs(dc) <= 1 && (dr || dc)) blocked8 += !fr;
+        }
+      float *x = feats_out + (size_t)k * kIn;
+      x[0] = c / 15.0f;                        // x
+      x[1] = r / 15.0f;                        // y
+      x[2] = blocked8 / 8.0f;                  // obstacle context: blocked or outside among the 8 neighbours
+      x[3] = cs / 15.0f;
+      x[4] = rs / 15.0f;
+      x[5] = W / 16.0f;
+      x[6] = H / 16.0f;
+      x[7] = C / 256.0f;
+      x[8] = (c - cs) / 15.0f;
+      x[9] = (r - rs) / 15.0f;
+      x[10] = W > 1 ? c / (float)(W - 1) : 0.0f;
+      x[11] = H > 1 ? r / (float)(H - 1) : 0.0f;
+      x[12] = free25 / 25.0f;
+      x[13] = (float)(r & 1);
+      x[14] = 1.0f;
+      x[15] = 0.0f;
+      ++k;
+    }
+  return QP_OK;
+}
+
+// ----------------------------------------------------------------------------- decode
+extern "C" qp_status qp_ws_decode(const float *logits, int32_t ld, int32_t C, int32_t start_cell, uint8_t *state_out,
+                                  int32_t *path_out) {
+  if (!logits || C < 1 || C > kOut || start_cell < 0 || start_cell >= C || ld < C)
+    return set_error(QP_EINVAL, "bad argument");
+  // Greedy matching: the start cell takes step 0; then repeatedly the largest
+  // logit among unassigned cells and free steps 1..C-1 fixes one (cell, step)
+  // pair (ties: smaller cell, then smaller step).  Each unassigned cell keeps
+  // its best free step; only cells whose best step was just taken rescan.
+  std::vector<int32_t> path(C, -1), best(C, -1);
+  std::vector<char> cell_done(C, 0), step_done(C, 0);
+  path[0] = start_cell;
+  cell_done[start_cell] = 1;
+  step_done[0] = 1;
+  auto rescan = [&](int i) {
+    int bt = -1;
+    float bv = 0.0f;
+    for (int t = 1; t < C; ++t) {
+      if (step_done[t]) continue;
+      const float v = logits[(size_t)i * ld + t];
+      if (bt < 0 || v > bv) {
+        bt = t;
+        bv = v;
+      }
+    }
+    best[i] = bt;
+  };
+  for (int i = 0; i < C; ++i)
+    if (!cell_done[i]) rescan(i);
+  for (int round = 1; round < C; ++round) {
+    int bi = -1;
+    float bv = 0.0f;
+    for (int i = 0; i < C; ++i) {
+      if (cell_done[i]) continue;
+      const float v = logits[(size_t)i * ld + best[i]];
+      if (bi < 0 || v > bv || (v == bv && i < bi)) {
+        bi = i;
+        bv = v;
+      }
+    }
+    const int t = best[bi];
+    path[t] = bi;
+    cell_done[bi] = 1;
+    step_done[t] = 1;
+    for (int i = 0; i < C; ++i)
+      if (!cell_done[i] && best[i] == t) rescan(i);
+  }
+  if (state_out) {
+    std::memset(state_out, 0, (size_t)C * C);
+    for (int t = 0; t < C; ++t) state_out[(size_t)t * C + path[t]] = 1;
+  }
+  if (path_out) std::memcpy(path_out, path.data(), (size_t)C * 4);
+  return QP_OK;
+}

@@ -27,7 +27,9 @@ E_NONE = np.iinfo(np.int64).max
 SYMBOLS = ["qp_build_qubo", "qp_build_from_dense", "qp_qubo_info", "qp_export_dense", "qp_export_dist",
            "qp_thresholds", "qp_anneal", "qp_anneal_ex", "qp_anneal_noalloc", "qp_batch_create",
            "qp_batch_run", "qp_batch_info", "qp_batch_destroy", "qp_anneal_batch", "qp_decode_path",
-           "qp_decode_batch", "qp_destroy", "qp_last_error"]
+           "qp_decode_batch", "qp_ws_create", "qp_ws_destroy", "qp_ws_param_count", "qp_ws_get_params",
+           "qp_ws_set_params", "qp_ws_features", "qp_ws_forward", "qp_ws_grads", "qp_ws_train_step",
+           "qp_ws_decode", "qp_destroy", "qp_last_error"]
 
 
 class QpError(RuntimeError):
@@ -84,6 +86,14 @@ def lib():
                 "qp_batch_run": [vp, vp],
                 "qp_batch_info": [vp, P(i32), P(i32), P(i32)],
                 "qp_anneal_batch": [P(vp), i32, i32, P(qp_schedule), u64, P(vp), P(vp), P(vp), vp],
+                "qp_ws_create": [u64, P(vp)],
+                "qp_ws_get_params": [vp, vp],
+                "qp_ws_set_params": [vp, vp],
+                "qp_ws_features": [P(qp_field), vp, P(i32)],
+                "qp_ws_forward": [vp, vp, i32, vp, vp],
+                "qp_ws_grads": [vp, vp, vp, vp, i32, vp, vp, vp],
+                "qp_ws_train_step": [vp, vp, vp, vp, i32, ct.c_float, vp, vp],
+                "qp_ws_decode": [vp, i32, i32, i32, vp, vp],
                 "qp_decode_path": [vp, vp, vp, vp],
                 "qp_decode_batch": [vp, i32, vp, vp, vp, vp],
             }
@@ -91,6 +101,10 @@ def lib():
                 fn = getattr(L, name)
                 fn.argtypes = args
                 fn.restype = ct.c_int
+            L.qp_ws_destroy.argtypes = [vp]
+            L.qp_ws_destroy.restype = None
+            L.qp_ws_param_count.argtypes = []
+            L.qp_ws_param_count.restype = i64
             L.qp_batch_destroy.argtypes = [vp]
             L.qp_batch_destroy.restype = None
             L.qp_destroy.argtypes = [vp]
@@ -316,3 +330,91 @@ def qp_decode_batch(h: Handle, replicas, states, paths_out, lengths_out, stream=
 
 def qp_destroy(h: Handle):
     h.close()
+
+
+# --------------------------------------------------------------------------- learned warm start
+WS_FEATURES, WS_STEPS = 16, 256
+
+
+class WarmStartModel:
+    """Owns a qp_ws* (the per-cell step-logit MLP)."""
+
+    def __init__(self, seed=0):
+        out = ct.c_void_p()
+        _check(lib().qp_ws_create(ct.c_uint64(seed), ct.byref(out)))
+        self.ptr = out
+
+    def close(self):
+        if self.ptr:
+            lib().qp_ws_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def qp_ws_param_count() -> int:
+    return int(lib().qp_ws_param_count())
+
+
+def qp_ws_get_params(m: WarmStartModel) -> np.ndarray:
+    out = np.zeros(qp_ws_param_count(), np.float32)
+    _check(lib().qp_ws_get_params(m.ptr, _ptr(out)))
+    return out
+
+
+def qp_ws_set_params(m: WarmStartModel, params):
+    p = np.ascontiguousarray(params, np.float32)
+    assert p.size == qp_ws_param_count()
+    _check(lib().qp_ws_set_params(m.ptr, _ptr(p)))
+
+
+def qp_ws_features(field) -> np.ndarray:
+    mask = None if field.free_mask is None else np.ascontiguousarray(field.free_mask, np.uint8)
+    f = qp_field(int(field.rows), int(field.cols), None if mask is None else mask.ctypes.data, int(field.start))
+    C = ct.c_int32()
+    _check(lib().qp_ws_features(ct.byref(f), None, ct.byref(C)))
+    out = np.zeros((C.value, WS_FEATURES), np.float32)
+    _check(lib().qp_ws_features(ct.byref(f), _ptr(out), ct.byref(C)))
+    return out
+
+
+def qp_ws_forward(m: WarmStartModel, feats, logits_out=None, stream=None):
+    x = np.ascontiguousarray(feats, np.float32)
+    M = x.shape[0]
+    out = np.zeros((M, WS_STEPS), np.float32) if logits_out is None else logits_out
+    _check(lib().qp_ws_forward(m.ptr, _ptr(x), M, _ptr(out), _stream(stream)))
+    return out
+
+
+def qp_ws_grads(m: WarmStartModel, feats, labels, steps, stream=None):
+    x = np.ascontiguousarray(feats, np.float32)
+    lb = np.ascontiguousarray(labels, np.int32)
+    sp = np.ascontiguousarray(steps, np.int32)
+    g = np.zeros(qp_ws_param_count(), np.float32)
+    loss = ct.c_float()
+    _check(lib().qp_ws_grads(m.ptr, _ptr(x), _ptr(lb), _ptr(sp), x.shape[0], _ptr(g), ct.byref(loss),
+                             _stream(stream)))
+    return loss.value, g
+
+
+def qp_ws_train_step(m: WarmStartModel, feats, labels, steps, lr, stream=None) -> float:
+    x = np.ascontiguousarray(feats, np.float32)
+    lb = np.ascontiguousarray(labels, np.int32)
+    sp = np.ascontiguousarray(steps, np.int32)
+    loss = ct.c_float()
+    _check(lib().qp_ws_train_step(m.ptr, _ptr(x), _ptr(lb), _ptr(sp), x.shape[0], ct.c_float(lr), ct.byref(loss),
+                                  _stream(stream)))
+    return loss.value
+
+
+def qp_ws_decode(logits, C, start_cell):
+    """-> (state uint8 [C*C], path int32 [C])"""
+    L = np.ascontiguousarray(logits, np.float32)
+    st = np.zeros(C * C, np.uint8)
+    path = np.zeros(C, np.int32)
+    _check(lib().qp_ws_decode(_ptr(L), L.shape[1], int(C), int(start_cell), _ptr(st), _ptr(path)))
+    return st, path

@@ -1,0 +1,92 @@
+"""The warm-start MLP on the GPU (tcgen05 GEMMs) against the CPU reference:
+logits within 2e-2 max-abs, gradients within 1e-2 relative per tensor."""
+import numpy as np
+import pytest
+
+from conftest import has_gpu
+from oracle import mlp_ref
+from paper_2608_25376_gb300 import build as qbuild
+from paper_2608_25376_gb300 import inputs, qpath
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not has_gpu():
+        pytest.skip("no CUDA device")
+    qbuild.build()
+    qpath.lib()
+
+
+def field_batch(n, seed):
+    """Features, labels (a serpentine-like order) and steps of n synthetic fields."""
+    fs = inputs.batch(n, seed=seed, lo=4, hi=12)
+    X, Y, T = [], [], []
+    for f in fs:
+        x = qpath.qp_ws_features(f)
+        C = x.shape[0]
+        X.append(x)
+        T.append(np.full(C, C, np.int32))
+        Y.append(np.argsort(np.argsort(x[:, 1] * 16 + x[:, 0])).astype(np.int32))
+    return np.concatenate(X), np.concatenate(Y), np.concatenate(T)
+
+
+def test_forward_logits_match_cpu(dev):
+    m = qpath.WarmStartModel(seed=5)
+    params = qpath.qp_ws_get_params(m)
+    X, _, _ = field_batch(5, seed=1)
+    X = X[:300]                                   # ragged: 300 rows, tiles of 128
+    got = qpath.qp_ws_forward(m, X)
+    ref, _ = mlp_ref.forward(params, X, bf16_storage=True)
+    err = np.abs(got - ref).max()
+    assert err <= 2e-2, err
+    assert np.abs(ref).max() > 0.1                # not a vacuous comparison
+
+
+def test_gradients_match_cpu(dev):
+    m = qpath.WarmStartModel(seed=6)
+    params = qpath.qp_ws_get_params(m)
+    X, Y, T = field_batch(8, seed=2)
+    Y[::7] = -1                                   # ignored rows
+    loss, g = qpath.qp_ws_grads(m, X, Y, T)
+    ref_loss, ref_g = mlp_ref.loss_and_grads(params, X, Y, T, bf16_storage=True)
+    assert abs(loss - ref_loss) <= 1e-3 * abs(ref_loss)
+    offs = np.cumsum([0] + [x for (no, ni) in mlp_ref.DIMS for x in (no * ni, no)])
+    for k in range(len(offs) - 1):
+        a, b = g[offs[k]:offs[k + 1]], ref_g[offs[k]:offs[k + 1]]
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        assert rel <= 1e-2, (k, rel)
+    # and against the exact float64 network, looser (bf16 storage in between)
+    _, g64 = mlp_ref.loss_and_grads(params, X, Y, T, bf16_storage=False)
+    rel = np.linalg.norm(g - g64) / np.linalg.norm(g64)
+    assert rel <= 5e-2, rel
+
+
+def test_large_batch_split_k(dev):
+    """8960 rows: 70 row tiles forward, 17-way split-K for the weight gradients."""
+    m = qpath.WarmStartModel(seed=7)
+    params = qpath.qp_ws_get_params(m)
+    X, Y, T = field_batch(140, seed=3)
+    X, Y, T = X[:8960], Y[:8960], T[:8960]
+    got = qpath.qp_ws_forward(m, X)
+    rows = np.random.default_rng(0).choice(len(X), 400, replace=False)
+    ref, _ = mlp_ref.forward(params, X[rows], bf16_storage=True)
+    assert np.abs(got[rows] - ref).max() <= 2e-2
+    loss, g = qpath.qp_ws_grads(m, X, Y, T)
+    ref_loss, ref_g = mlp_ref.loss_and_grads(params, X, Y, T, bf16_storage=True)
+    assert np.linalg.norm(g - ref_g) / np.linalg.norm(ref_g) <= 1e-2
+
+
+def test_training_reduces_loss(dev):
+    m = qpath.WarmStartModel(seed=8)
+    X, Y, T = field_batch(40, seed=4)
+    first = qpath.qp_ws_train_step(m, X, Y, T, 1e-3)
+    for _ in range(80):
+        last = qpath.qp_ws_train_step(m, X, Y, T, 1e-3)
+    assert last < 0.6 * first, (first, last)
+    # the updated weights still give CPU-matching logits
+    params = qpath.qp_ws_get_params(m)
+    got = qpath.qp_ws_forward(m, X[:256])
+    ref, _ = mlp_ref.forward(params, X[:256], bf16_storage=True)
+    assert np.abs(got - ref).max() <= 2e-2 * max(1.0, np.abs(ref).max() / 10)
