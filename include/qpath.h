@@ -271,6 +271,14 @@ qp_status qp_ws_train_step(qp_ws *ws, const float *feats, const int32_t *labels,
 qp_status qp_ws_decode(const float *logits, int32_t ld, int32_t C, int32_t start_cell, uint8_t *state_out,
                        int32_t *path_out);
 
+/* Logits of one field's C cells -> a feasible state by a guided walk: from
+ * the start cell, each step goes to the nearest unvisited cell (d: the C x C
+ * distance matrix, host, e.g. from qp_export_dist); among equally near cells
+ * the one with the smallest expected step E_j = sum_t softmax(logits_j)_t t
+ * (t < C) wins, then the smaller cell id.  Either output may be NULL. */
+qp_status qp_ws_decode_walk(const float *logits, int32_t ld, int32_t C, int32_t start_cell, const int32_t *d,
+                            uint8_t *state_out, int32_t *path_out);
+
 /* Free a handle and its device memory (NULL is ignored). */
 void qp_destroy(qp_handle *h);
 

@@ -109,3 +109,22 @@ def greedy_decode(logits, C, start_cell):
         cells.remove(i)
         steps.remove(t)
     return path
+
+
+def walk_decode(logits, C, start_cell, d):
+    """From the start cell, step to the nearest unvisited cell; ties by the
+    smaller expected step under softmax over t < C, then the smaller cell."""
+    L = np.asarray(logits, dtype=np.float64)[:C, :C]
+    e = []
+    for i in range(C):
+        z = L[i] - L[i].max()
+        p = np.exp(z)
+        e.append(float((p * np.arange(C)).sum() / p.sum()))
+    path, seen, cur = [start_cell], {start_cell}, start_cell
+    for _ in range(1, C):
+        cands = [j for j in range(C) if j not in seen]
+        nxt = min(cands, key=lambda j: (int(d[cur][j]), e[j], j))
+        path.append(nxt)
+        seen.add(nxt)
+        cur = nxt
+    return path

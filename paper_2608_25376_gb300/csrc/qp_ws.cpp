@@ -484,3 +484,52 @@ extern "C" qp_status qp_ws_decode(const float *logits, int32_t ld, int32_t C, in
   if (path_out) std::memcpy(path_out, path.data(), (size_t)C * 4);
   return QP_OK;
 }
+
+// A walk guided by the predicted steps: from the start cell, move each step to
+// the unvisited cell nearest to the current one (distance matrix d), choosing
+// among equally near cells the one with the smallest expected step
+// E_j = sum_t softmax(logits_j)_t * t over t < C (then the smaller cell id).
+extern "C" qp_status qp_ws_decode_walk(const float *logits, int32_t ld, int32_t C, int32_t start_cell,
+                                       const int32_t *d, uint8_t *state_out, int32_t *path_out) {
+  if (!logits || !d || C < 1 || C > kOut || start_cell < 0 || start_cell >= C || ld < C)
+    return set_error(QP_EINVAL, "bad argument");
+  std::vector<double> e(C);
+  for (int i = 0; i < C; ++i) {
+    const float *z = logits + (size_t)i * ld;
+    double mx = z[0];
+    for (int t = 1; t < C; ++t) mx = std::max(mx, (double)z[t]);
+    double s = 0.0, st = 0.0;
+    for (int t = 0; t < C; ++t) {
+      const double p = std::exp((double)z[t] - mx);
+      s += p;
+      st += p * t;
+    }
+    e[i] = st / s;
+  }
+  std::vector<int32_t> path(C);
+  std::vector<char> seen(C, 0);
+  int cur = start_cell;
+  path[0] = cur;
+  seen[cur] = 1;
+  for (int t = 1; t < C; ++t) {
+    int nb = -1;
+    for (int j = 0; j < C; ++j) {
+      if (seen[j]) continue;
+      if (nb < 0) {
+        nb = j;
+        continue;
+      }
+      const int32_t dj = d[(size_t)cur * C + j], db = d[(size_t)cur * C + nb];
+      if (dj < db || (dj == db && e[j] < e[nb])) nb = j;
+    }
+    path[t] = nb;
+    seen[nb] = 1;
+    cur = nb;
+  }
+  if (state_out) {
+    std::memset(state_out, 0, (size_t)C * C);
+    for (int t = 0; t < C; ++t) state_out[(size_t)t * C + path[t]] = 1;
+  }
+  if (path_out) std::memcpy(path_out, path.data(), (size_t)C * 4);
+  return QP_OK;
+}

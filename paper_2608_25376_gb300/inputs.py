@@ -11,6 +11,9 @@ Table II; it names no dataset):
   * ``obstacles`` -- M x N grid, each cell an obstacle with probability p
                      (independent draws from numpy's PCG64 seeded with ``seed``);
                      the start cell is forced free.
+  * ``fields_8_16`` -- rectangles with sides in [8, 16] (or fixed squares) and
+                     obstacle probability uniform in [0, 0.2]; start = first
+                     free cell.  Training seeds and held-out seeds are disjoint.
   * ``batch``     -- ``count`` fields with sides H, W uniform in [lo, hi],
                      obstacle probability uniform in [0, p_max], and an
                      irregular boundary: each row loses 0..floor(W/4) cells at
@@ -69,6 +72,26 @@ def batch(count: int, seed: int, lo: int = 4, hi: int = 16, p_max: float = 0.2) 
             flat[:2] = 1
             free = np.flatnonzero(flat)
         out.append(Field(H, W, flat.astype(np.uint8), int(free[0])))
+    return out
+
+
+def fields_8_16(count: int, seed: int, lo: int = 8, hi: int = 16, p_max: float = 0.2,
+                square: int = 0) -> list[Field]:
+    """Rectangles with sides uniform in [lo, hi] (or square x square when
+    square > 0) and obstacle probability uniform in [0, p_max]; the start is the
+    first free cell in row-major order."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        H = square or int(rng.integers(lo, hi + 1))
+        W = square or int(rng.integers(lo, hi + 1))
+        p = float(rng.uniform(0.0, p_max))
+        mask = (rng.random(H * W) >= p).astype(np.uint8)
+        free = np.flatnonzero(mask)
+        if free.size < 2:
+            mask[:2] = 1
+            free = np.flatnonzero(mask)
+        out.append(Field(H, W, mask, int(free[0])))
     return out
 
 

@@ -29,7 +29,7 @@ SYMBOLS = ["qp_build_qubo", "qp_build_from_dense", "qp_qubo_info", "qp_export_de
            "qp_batch_run", "qp_batch_info", "qp_batch_destroy", "qp_anneal_batch", "qp_decode_path",
            "qp_decode_batch", "qp_ws_create", "qp_ws_destroy", "qp_ws_param_count", "qp_ws_get_params",
            "qp_ws_set_params", "qp_ws_features", "qp_ws_forward", "qp_ws_grads", "qp_ws_train_step",
-           "qp_ws_decode", "qp_destroy", "qp_last_error"]
+           "qp_ws_decode", "qp_ws_decode_walk", "qp_destroy", "qp_last_error"]
 
 
 class QpError(RuntimeError):
@@ -94,6 +94,7 @@ def lib():
                 "qp_ws_grads": [vp, vp, vp, vp, i32, vp, vp, vp],
                 "qp_ws_train_step": [vp, vp, vp, vp, i32, ct.c_float, vp, vp],
                 "qp_ws_decode": [vp, i32, i32, i32, vp, vp],
+                "qp_ws_decode_walk": [vp, i32, i32, i32, vp, vp, vp],
                 "qp_decode_path": [vp, vp, vp, vp],
                 "qp_decode_batch": [vp, i32, vp, vp, vp, vp],
             }
@@ -417,4 +418,14 @@ def qp_ws_decode(logits, C, start_cell):
     st = np.zeros(C * C, np.uint8)
     path = np.zeros(C, np.int32)
     _check(lib().qp_ws_decode(_ptr(L), L.shape[1], int(C), int(start_cell), _ptr(st), _ptr(path)))
+    return st, path
+
+
+def qp_ws_decode_walk(logits, C, start_cell, d):
+    """-> (state uint8 [C*C], path int32 [C]) by the guided nearest-cell walk"""
+    L = np.ascontiguousarray(logits, np.float32)
+    dd = np.ascontiguousarray(d, np.int32)
+    st = np.zeros(C * C, np.uint8)
+    path = np.zeros(C, np.int32)
+    _check(lib().qp_ws_decode_walk(_ptr(L), L.shape[1], int(C), int(start_cell), _ptr(dd), _ptr(st), _ptr(path)))
     return st, path

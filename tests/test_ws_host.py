@@ -83,3 +83,15 @@ def test_decode_matches_plain_greedy_and_is_a_path(L, C, seed):
     assert path.tolist() == mlp_ref.greedy_decode(logits, C, start)
     x = st.reshape(C, C)
     assert (x.sum(axis=0) == 1).all() and (x.sum(axis=1) == 1).all() and x[0, start] == 1
+
+
+@pytest.mark.parametrize("shape,seed", [((3, 4), 0), ((6, 7), 1), ((9, 9), 2)])
+def test_walk_decode_matches_plain_restatement(L, orc, shape, seed):
+    f = inputs.obstacles(*shape, 0.15, seed=seed)
+    P = orc.Problem(f.rows, f.cols, f.free_mask, f.start)
+    rng = np.random.default_rng(seed)
+    logits = rng.normal(size=(P.C, 256)).astype(np.float32)
+    st, path = qpath.qp_ws_decode_walk(logits, P.C, P.start_cell, P.d)
+    assert path.tolist() == mlp_ref.walk_decode(logits, P.C, P.start_cell, P.d)
+    x = st.reshape(P.C, P.C)
+    assert (x.sum(axis=0) == 1).all() and (x.sum(axis=1) == 1).all() and x[0, P.start_cell] == 1
