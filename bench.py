@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-warm-start", action="store_true")
     ap.add_argument("--replicas-per-cta", type=int, default=0)
     ap.add_argument("--structured-kernel", default="rows", choices=["rows", "flat"])
     ap.add_argument("--profile-case", default=None, choices=["rows", "flat", "dense"],
@@ -150,23 +151,25 @@ class Clocks:
 
 def cpu_baseline(w, P, max_seconds=20.0):
     """The oracle as it stands on this host's cores, on a bounded sample of the
-    workload: `cores` replicas, each through a prefix of the sweeps sized to about
-    max_seconds of CPU work (all sweeps when that fits)."""
+    workload: about max_seconds of CPU work, one thread per replica, each
+    replica through all sweeps when that fits (else a sweep prefix)."""
     import oracle
     cores = os.cpu_count() or 1
     S = w["n_sweeps"]
-    # size the sweep count from a short probe
-    probe_s = max(1, min(S, 50))
+    probe_s = max(1, min(S, 100))
     t = time.perf_counter()
     oracle.anneal_structured(P, 1, S, seed=w["seed"], sweep_end=probe_s, n_threads=1)
-    per_sweep = (time.perf_counter() - t) / probe_s
-    sweeps = int(max(1, min(S, max_seconds / max(per_sweep, 1e-9))))
+    per_sweep = max((time.perf_counter() - t) / probe_s, 1e-9)
+    sweeps = int(max(1, min(S, max_seconds / per_sweep)))
+    waves = int(max(1, min(max(1, w["replicas"] // cores), max_seconds / (per_sweep * sweeps))))
+    reps = cores * waves
     t = time.perf_counter()
-    oracle.anneal_structured(P, cores, S, seed=w["seed"], sweep_end=sweeps, n_threads=cores)
+    oracle.anneal_structured(P, reps, S, seed=w["seed"], sweep_end=sweeps, n_threads=cores)
     dt = time.perf_counter() - t
-    attempts = cores * sweeps * (P.C - 1) ** 2
+    attempts = reps * sweeps * (P.C - 1) ** 2
     return {"value": attempts / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{cores} replicas x sweeps [0,{sweeps}) of {S}, {P.C} cells, one thread per replica",
+            "sample": f"{reps} of {w['replicas']} replicas x sweeps [0,{sweeps}) of {S}, {P.C} cells, "
+                      f"one thread per replica",
             "seconds": round(dt, 2)}
 
 
@@ -246,6 +249,30 @@ def bench_batch(args, flush, stream):
             "feasible_replicas": feas}
 
 
+def bench_warm_start():
+    """Time to within 1% of the best known path, learned warm start vs plain
+    annealing, on 4 held-out 16x16 fields (1024 replicas x 2000 sweeps per arm,
+    25% seeded).  A reduced training set keeps the bench short: labels from 1024
+    seeded 8..16 fields (32 replicas x 2000 sweeps each), 8 epochs; the
+    10000-field workload is `python -m paper_2608_25376_gb300.warmstart`."""
+    from paper_2608_25376_gb300 import inputs, qpath, warmstart
+    t = time.perf_counter()
+    data = warmstart.annealer_labels(inputs.fields_8_16(1024, seed=1000), replicas=32, n_sweeps=2000)
+    m = qpath.WarmStartModel(seed=1)
+    losses = warmstart.train(m, data, epochs=8)
+    prep = time.perf_counter() - t
+    ev = inputs.fields_8_16(4, seed=999999, square=16)
+    rows = warmstart.evaluate(m, ev, replicas=1024, n_sweeps=2000, ref_sweeps=5000)
+    s = warmstart.summarize(rows)
+    return {"metric": "seconds to within 1% of the best known path (mean over fields that reached it)",
+            "learned_s": s["learned"]["mean_s"], "learned_reached": f'{s["learned"]["reached"]}/{s["learned"]["of"]}',
+            "plain_s": s["plain"]["mean_s"], "plain_reached": f'{s["plain"]["reached"]}/{s["plain"]["of"]}',
+            "plain_final_gap": s["mean_gap_plain_final"], "learned_seed_gap": s["mean_gap_seed"],
+            "fields": "4 held-out 16x16 (seed 999999), A = 2 max d, 1024 replicas x 2000 sweeps per arm",
+            "training": f"{len(data)} fields, {len(losses)} steps, loss {losses[0]:.3f} -> {losses[-1]:.3f}, "
+                        f"labels+training {prep:.1f} s"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -283,7 +310,8 @@ def run_ours(args):
     paths = torch.zeros((R, C), dtype=torch.int32, device=dev)
     lens = torch.zeros(R, dtype=torch.int64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-    offset = rank * R
+    from paper_2608_25376_gb300 import shard
+    offset, _ = shard.replica_range(rank, world, R, "weak")
     rpc = args.replicas_per_cta
     skernel = qpath.QP_KERNEL_STRUCTURED if args.structured_kernel == "rows" else qpath.QP_KERNEL_STRUCTURED_FLAT
 
@@ -327,6 +355,8 @@ def run_ours(args):
     value = world * attempts / (ms_max / 1e3)
     feasible = int((lens >= 0).sum().item())
     best_len = int(lens[lens >= 0].min().item()) if feasible else None
+    best_len = shard.reduce_best(best_len if best_len is not None else np.iinfo(np.int64).max)
+    best_len = None if best_len == np.iinfo(np.int64).max else best_len
 
     pk, pk_kind = peaks()
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
@@ -378,6 +408,9 @@ def run_ours(args):
 
     if not args.no_batch and rank == 0:
         line.setdefault("variants", {})["batched"] = bench_batch(args, flush, stream)
+
+    if not args.no_warm_start and rank == 0:
+        line["warm_start"] = bench_warm_start()
 
     if not args.no_e2e:
         pin_states = torch.empty((R, n), dtype=torch.uint8, pin_memory=True)
