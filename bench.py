@@ -161,7 +161,10 @@ def cpu_baseline(w, P, max_seconds=20.0):
     oracle.anneal_structured(P, 1, S, seed=w["seed"], sweep_end=probe_s, n_threads=1)
     per_sweep = max((time.perf_counter() - t) / probe_s, 1e-9)
     sweeps = int(max(1, min(S, max_seconds / per_sweep)))
-    waves = int(max(1, min(max(1, w["replicas"] // cores), max_seconds / (per_sweep * sweeps))))
+    t = time.perf_counter()  # one replica through the chosen sweeps sizes the number of waves
+    oracle.anneal_structured(P, [w["replicas"] - 1], S, seed=w["seed"], sweep_end=sweeps, n_threads=1)
+    one = max(time.perf_counter() - t, 1e-9)
+    waves = int(max(1, min(max(1, w["replicas"] // cores), max_seconds / one)))
     reps = cores * waves
     t = time.perf_counter()
     oracle.anneal_structured(P, reps, S, seed=w["seed"], sweep_end=sweeps, n_threads=cores)
