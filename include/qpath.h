@@ -83,10 +83,21 @@ typedef struct {
 
 /* qp_build_qubo flags */
 enum { QP_DENSE = 1, QP_STRUCTURED = 2, QP_DIST_I16 = 4 };
-/* qp_anneal_opts.kernel.  STRUCTURED uses the row-parallel kernel for fields of
- * up to 512 cells and the general one above; STRUCTURED_FLAT forces the general
- * structured kernel (any field up to 4096 cells). */
-enum { QP_KERNEL_AUTO = 0, QP_KERNEL_DENSE = 1, QP_KERNEL_STRUCTURED = 2, QP_KERNEL_STRUCTURED_FLAT = 3 };
+/* qp_anneal_opts.kernel.  STRUCTURED uses the row-parallel kernel for fields
+ * of up to 512 cells and the general one above; STRUCTURED_ROWS forces the
+ * row-parallel kernel (up to 512 cells), STRUCTURED_FLAT the general structured
+ * kernel (up to 4096 cells), STRUCTURED_GROUP the grouped kernel that anneals 4
+ * replicas per warp up to 64 cells and 2 up to 128 (faster than the
+ * row-parallel kernel at low temperature, slower at high temperature).  All
+ * give the same results. */
+enum {
+  QP_KERNEL_AUTO = 0,
+  QP_KERNEL_DENSE = 1,
+  QP_KERNEL_STRUCTURED = 2,
+  QP_KERNEL_STRUCTURED_FLAT = 3,
+  QP_KERNEL_STRUCTURED_ROWS = 4,
+  QP_KERNEL_STRUCTURED_GROUP = 5
+};
 
 typedef struct {
   int32_t kernel;            /* QP_KERNEL_*; AUTO = structured when built     */

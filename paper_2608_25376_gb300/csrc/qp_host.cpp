@@ -445,11 +445,11 @@ extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc
     return fail(QP_EINVAL, "replica_offset out of range");
   int kernel = o.kernel;
   if (kernel == QP_KERNEL_AUTO) kernel = h->path ? QP_KERNEL_STRUCTURED : QP_KERNEL_DENSE;
-  if ((kernel == QP_KERNEL_STRUCTURED || kernel == QP_KERNEL_STRUCTURED_FLAT) && !h->path)
-    return fail(QP_EINVAL, "no structured form in this handle");
+  const bool structured = kernel == QP_KERNEL_STRUCTURED || kernel == QP_KERNEL_STRUCTURED_FLAT ||
+                          kernel == QP_KERNEL_STRUCTURED_ROWS || kernel == QP_KERNEL_STRUCTURED_GROUP;
+  if (structured && !h->path) return fail(QP_EINVAL, "no structured form in this handle");
   if (kernel == QP_KERNEL_DENSE && !h->has_dense) return fail(QP_EINVAL, "handle was built without QP_DENSE");
-  if (kernel != QP_KERNEL_STRUCTURED && kernel != QP_KERNEL_DENSE && kernel != QP_KERNEL_STRUCTURED_FLAT)
-    return fail(QP_EINVAL, "unknown kernel %d", kernel);
+  if (!structured && kernel != QP_KERNEL_DENSE) return fail(QP_EINVAL, "unknown kernel %d", kernel);
   if (o.replicas_per_cta < 0 || o.replicas_per_cta > kMaxWarpsPerCta)
     return fail(QP_EINVAL, "replicas_per_cta must be in [0, %d]", kMaxWarpsPerCta);
 
@@ -479,7 +479,7 @@ extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc
   const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
 
   LaunchInfo info;
-  if (kernel == QP_KERNEL_STRUCTURED || kernel == QP_KERNEL_STRUCTURED_FLAT) {
+  if (structured) {
     int W = o.replicas_per_cta ? o.replicas_per_cta : 4;
     StructArgs a{};
     a.C = h->C; a.Cp = h->Cp; a.start = h->start; a.A = h->A; a.B = h->B;
@@ -489,7 +489,15 @@ extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc
     a.key0 = key0; a.key1 = key1;
     a.thr = sched.thr; a.thr_off = sched.off; a.thr_len = sched.len; a.thr_c = sched.c;
     a.init = init_d; a.states_out = st_d; a.E_out = e_d; a.best_out = b_d; a.acc_out = a_d;
-    if (kernel == QP_KERNEL_STRUCTURED) {
+    if (kernel == QP_KERNEL_STRUCTURED_GROUP) {
+      if (group_size_for(h->C) < 2) return fail(QP_EINVAL, "the grouped kernel takes fields of up to 128 cells");
+      int Wg = W;
+      while (Wg > 1 && !group_supported(h->C, h->d_i16, Wg)) --Wg;
+      if (!group_supported(h->C, h->d_i16, Wg)) return fail(QP_ERANGE, "grouped kernel: no launch fits");
+      QP_CU(launch_group(a, h->d_i16, Wg, st, &info));
+      goto launched;
+    }
+    if (kernel == QP_KERNEL_STRUCTURED || kernel == QP_KERNEL_STRUCTURED_ROWS) {
       int Wr = W;
       while (Wr > 1 && !rows_supported(h->C, h->d_i16, Wr)) --Wr;
       if (rows_supported(h->C, h->d_i16, Wr)) {

@@ -88,6 +88,11 @@ bool batch_supported(int Cmax, int warps_per_cta);
 cudaError_t batch_prepare(int Cmax, int warps_per_cta, int *blocks_per_sm);
 cudaError_t launch_batch(const StructArgs *fields, const int2 *units, int n_units, int *counter, int Cmax,
                          int warps_per_cta, int blocks, cudaStream_t st);
+// Grouped structured kernel (qp_sweep_group.cu): 4 replicas per warp for
+// C <= 64, 2 for C <= 128.
+int group_size_for(int C);
+bool group_supported(int C, bool d_i16, int warps_per_cta);
+cudaError_t launch_group(const StructArgs &a, bool d_i16, int warps_per_cta, cudaStream_t st, LaunchInfo *info);
 cudaError_t launch_dense(const DenseArgs &a, bool s_i16, int warps_per_cta, cudaStream_t st,
                          LaunchInfo *info);
 bool dense_h_fits_smem(int64_t n, int C, int warps_per_cta);

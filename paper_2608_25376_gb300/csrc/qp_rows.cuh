@@ -1,0 +1,265 @@
+// Device helpers of the row-parallel structured sweeps (qp_sweep_rows.cu,
+// qp_sweep_dual.cu): distance-row loads, row fields, the single-cell cache
+// and the evaluation of one row chunk.  Included inside namespace qp::{anon}.
+#pragma once
+
+__host__ __device__ constexpr size_t align16r(size_t x) { return (x + 15) & ~size_t(15); }
+
+// d modes: 0 = global memory (DT), 1 = shared memory (DT), 2 = shared memory widened to int32
+template <typename DT, int DMODE>
+__device__ __forceinline__ void drow4(const void *d, int Cp, int h, int i, bool ok, int (&v)[4]) {
+  v[0] = v[1] = v[2] = v[3] = 0;
+  if (!ok) return;
+  if (DMODE == 2) {
+    const int4 q = *reinterpret_cast<const int4 *>(static_cast<const int *>(d) + (size_t)h * Cp + i);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else if (sizeof(DT) == 2) {
+    const uint2 *p = reinterpret_cast<const uint2 *>(static_cast<const DT *>(d) + (size_t)h * Cp + i);
+    const uint2 q = DMODE == 1 ? *p : __ldg(p);
+    v[0] = (int)(short)(q.x & 0xFFFFu);
+    v[1] = (int)q.x >> 16;
+    v[2] = (int)(short)(q.y & 0xFFFFu);
+    v[3] = (int)q.y >> 16;
+  } else {
+    const int4 *p = reinterpret_cast<const int4 *>(static_cast<const DT *>(d) + (size_t)h * Cp + i);
+    const int4 q = DMODE == 1 ? *p : __ldg(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  }
+}
+
+template <typename DT, int NCH, int DMODE>
+__device__ __forceinline__ void add_drow(const void *d, int Cp, int C, int h, int lane, int dlt,
+                                         int (&F)[NCH][4]) {
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    const int i = 128 * c + 4 * lane;
+    int v[4];
+    drow4<DT, DMODE>(d, Cp, h, i, i < C, v);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) F[c][j] += dlt * v[j];
+  }
+}
+
+// F += sum over the set bits h of one row of d[h][.]; returns the number of bits
+// and, in *one, the cell when there is exactly one (else -1).
+template <typename DT, int NCH, int DMODE>
+__device__ __forceinline__ int scan_row_field(const uint32_t *row, int Cw, const void *d, int Cp, int C,
+                                              int lane, int (&F)[NCH][4], int *one) {
+  const uint32_t word = lane < Cw ? row[lane] : 0u;
+  const int cnt = __reduce_add_sync(kFull, __popc(word));
+  uint32_t bal = __ballot_sync(kFull, word != 0u);
+  int last = -1;
+  while (bal) {
+    const int w = __ffs(bal) - 1;
+    bal &= bal - 1;
+    uint32_t wd = __shfl_sync(kFull, word, w);
+    while (wd) {
+      const int h = (w << 5) + __ffs(wd) - 1;
+      wd &= wd - 1;
+      last = h;
+      add_drow<DT, NCH, DMODE>(d, Cp, C, h, lane, 1, F);
+    }
+  }
+  *one = cnt == 1 ? last : -1;
+  return cnt;
+}
+
+// The single hot cell of a row, or -1 if the row does not hold exactly one.
+__device__ __forceinline__ int row_single(const uint32_t *row, int Cw, int lane) {
+  const uint32_t word = lane < Cw ? row[lane] : 0u;
+  const int cnt = __reduce_add_sync(kFull, __popc(word));
+  if (cnt != 1) return -1;
+  const uint32_t bal = __ballot_sync(kFull, word != 0u);
+  const int w = __ffs(bal) - 1;
+  const uint32_t wd = __shfl_sync(kFull, word, w);
+  return (w << 5) + __ffs(wd) - 1;
+}
+
+template <int NCH>
+__device__ __forceinline__ void zero(int (&F)[NCH][4]) {
+#pragma unroll
+  for (int c = 0; c < NCH; ++c)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) F[c][j] = 0;
+}
+
+__device__ __forceinline__ int sel4(const int (&v)[4], int j) {
+  return j == 0 ? v[0] : (j == 1 ? v[1] : (j == 2 ? v[2] : v[3]));
+}
+
+// The proposals of one 128-wide row chunk when at least one of them can be
+// accepted or needs a draw: evaluate against the current row sum, take the
+// first accepted one, apply it, resume after it.  Returns whether any flip was
+// applied.
+template <typename DT, int NCH, int DMODE>
+__device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int (&base)[4], int &xnc, int validc,
+                                       int (&tAc)[4], int &rt, int (&Cu)[NCH][4], uint32_t *row, long long &E,
+                                       long long &acc, int &viol, const void *d, int Cp, int C, int lane, int twoA,
+                                       int len, unsigned lenm1, float cT, const uint32_t *thr, uint32_t rg,
+                                       uint32_t key0, uint32_t key1) {
+  const int ib = 128 * c + 4 * lane;
+  const int delta = tC & 3;
+  int cand = validc;
+  bool h0 = false, h1 = false, flipped = false;
+  uint4 u0 = make_uint4(0, 0, 0, 0), u1 = make_uint4(0, 0, 0, 0);
+  while (true) {
+    const int k0 = twoA * (rt - 1), k1 = twoA * (3 - rt);
+    int accm = 0, need = 0, dE[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      dE[j] = ((xnc >> j) & 1) ? k1 - base[j] : base[j] + k0;
+      const unsigned dm1 = (unsigned)(dE[j] - 1);
+      accm |= (int)(dm1 >> 31) << j;   // dE <= 0
+      need |= (int)(dm1 < lenm1) << j;  // 1 <= dE < len
+    }
+    accm &= cand;
+    need &= cand;
+    if (__ballot_sync(kFull, need)) {
+      // lane L's proposals lie in counter blocks b0 and (when delta != 0) b0 + 1,
+      // which is lane L+1's b0: every lane computes its own block once and
+      // takes the next one from its right neighbour; lane 31 computes its
+      // second block itself when it needs it.
+      const int m0 = (1 << (4 - delta)) - 1;
+      const uint32_t b0 = (uint32_t)((tC + ib) >> 2);
+      if (!h0) {
+        u0 = philox4x32_10(make_uint4(b0, (uint32_t)s, rg, kRngTag), key0, key1);
+        u1.x = __shfl_down_sync(kFull, u0.x, 1);
+        u1.y = __shfl_down_sync(kFull, u0.y, 1);
+        u1.z = __shfl_down_sync(kFull, u0.z, 1);
+        u1.w = __shfl_down_sync(kFull, u0.w, 1);
+        h0 = true;
+      }
+      if (lane == 31 && (need & ~m0) && !h1) {
+        u1 = philox4x32_10(make_uint4(b0 + 1, (uint32_t)s, rg, kRngTag), key0, key1);
+        h1 = true;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if ((need >> j) & 1) {
+          const int wsel = (delta + j) & 3;
+          const uint32_t u = (j < 4 - delta) ? word_of(u0, wsel) : word_of(u1, wsel);
+          if (accept_draw(u, dE[j], cT, thr)) accm |= 1 << j;
+        }
+      }
+    }
+    const uint32_t bal = __ballot_sync(kFull, accm);
+    if (bal == 0) break;
+    const int L = __ffs(bal) - 1;
+    const int jl = accm ? __ffs(accm) - 1 : 0;
+    const int xl = (xnc >> jl) & 1;
+    const int tc = sel4(tAc, jl);
+    const int pk0 = jl | (xl << 2) | ((tc == twoA) << 3) | ((tc + (1 - 2 * xl) * twoA == twoA) << 4);
+    const int de = __shfl_sync(kFull, sel4(dE, jl), L);
+    const int pk = __shfl_sync(kFull, pk0, L);
+    const int jj = pk & 3, dlt = 1 - 2 * ((pk >> 2) & 1);
+    E += de;
+    ++acc;
+    rt += dlt;
+    viol += ((pk >> 4) & 1 ? 0 : 1) - ((pk >> 3) & 1 ? 0 : 1);
+    flipped = true;
+    if (lane == L) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j == jj) tAc[j] += dlt * twoA;
+      xnc ^= 1 << jj;
+      row[4 * c + (L >> 3)] ^= 1u << (4 * (L & 7) + jj);
+    }
+    add_drow<DT, NCH, DMODE>(d, Cp, C, 128 * c + 4 * L + jj, lane, dlt, Cu);
+    cand &= lane < L ? 0 : (lane > L ? 0xF : (0xF << (jj + 1)) & 0xF);
+    __syncwarp();
+  }
+  return flipped;
+}
+
+
+// The initial state of replica r (given or all zero, with row 0 and column s
+// clamped: x_{0,s} = 1), its single-cell cache, 2A x column sums, the mask
+// of proposable columns, its energy by Eqs. 3-6 and its violation count.
+template <typename DT, int NCH, int DMODE>
+__device__ __forceinline__ void rows_init(const StructArgs &a, int r, uint32_t *st, int16_t *hot1, const void *d,
+                                          int lane, int (&tAc)[NCH][4], int (&validc)[NCH], long long &E_out,
+                                          int &viol_out) {
+  const int C = a.C, Cp = a.Cp, s0 = a.start, A = a.A, B = a.B;
+  const int twoA = 2 * A;
+  const int Cw = (C + 31) >> 5;
+  const int n = C * C;
+  // ---- initial state: given or all zero; row 0 and column s clamped (x_{0,s} = 1)
+  const uint8_t *init = a.init ? a.init + (size_t)r * n : nullptr;
+  for (int e = lane; e < C * Cw; e += 32) {
+    const int t = e / Cw, w = e - t * Cw;
+    uint32_t word = 0;
+    if (t == 0) {
+      if ((s0 >> 5) == w) word = 1u << (s0 & 31);
+    } else if (init) {
+      for (int b = 0; b < 32; ++b) {
+        const int i = (w << 5) + b;
+        if (i < C && i != s0 && init[(size_t)t * C + i]) word |= 1u << b;
+      }
+    }
+    st[e] = word;
+  }
+  __syncwarp();
+
+  // ---- column sums, per-row single cells, penalties and H_dist (Eqs. 3-6)
+  int cs[NCH][4];
+  zero<NCH>(cs);
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    validc[c] = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = 128 * c + 4 * lane + j;
+      if (i < C && i != s0) validc[c] |= 1 << j;
+    }
+  }
+  long long hd = 0, pen_rows = 0;
+  int viol = 0;
+  {
+    int Fn[NCH][4];
+    for (int t = 0; t < C; ++t) {
+      const uint32_t *row = st + t * Cw;
+      int rsum = 0, xb[NCH];
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) {
+        const int ib = 128 * c + 4 * lane;
+        xb[c] = ib < C ? (int)((row[4 * c + (lane >> 3)] >> (4 * (lane & 7))) & 0xFu) : 0;
+        rsum += __popc(xb[c]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cs[c][j] += (xb[c] >> j) & 1;
+      }
+      rsum = __reduce_add_sync(kFull, rsum);
+      pen_rows += (long long)(1 - rsum) * (1 - rsum);
+      viol += rsum != 1;
+      const int h1 = row_single(row, Cw, lane);
+      if (lane == 0) hot1[t] = (int16_t)h1;
+      if (t + 1 < C) {
+        zero<NCH>(Fn);
+        int one;
+        scan_row_field<DT, NCH, DMODE>(st + (t + 1) * Cw, Cw, d, Cp, C, lane, Fn, &one);
+#pragma unroll
+        for (int c = 0; c < NCH; ++c)
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if ((xb[c] >> j) & 1) hd += Fn[c][j];
+      }
+    }
+  }
+  __syncwarp();
+  long long pen_cols = 0;
+  int viol_cols = 0;
+#pragma unroll
+  for (int c = 0; c < NCH; ++c)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (128 * c + 4 * lane + j < C) {
+        pen_cols += (long long)(1 - cs[c][j]) * (1 - cs[c][j]);
+        viol_cols += cs[c][j] != 1;
+      }
+  E_out = (long long)B * warp_sum64(hd) + (long long)A * (pen_rows + warp_sum64(pen_cols));
+  viol_out = viol + __reduce_add_sync(kFull, viol_cols);
+#pragma unroll
+  for (int c = 0; c < NCH; ++c)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) tAc[c][j] = twoA * cs[c][j];
+
+}

@@ -92,13 +92,24 @@ def test_build_matches_oracle(dev, orc, name, f):
 
 
 # ----------------------------------------------------------------- structured sweep
-STRUCT_KERNELS = [("rows", qpath.QP_KERNEL_STRUCTURED), ("flat", qpath.QP_KERNEL_STRUCTURED_FLAT)]
+STRUCT_KERNELS = [("rows", qpath.QP_KERNEL_STRUCTURED_ROWS), ("flat", qpath.QP_KERNEL_STRUCTURED_FLAT),
+                  ("group", qpath.QP_KERNEL_STRUCTURED_GROUP)]
+
+
+def kernel_fits(kernel, C):
+    if kernel == qpath.QP_KERNEL_STRUCTURED_GROUP:
+        return C <= 128
+    if kernel == qpath.QP_KERNEL_STRUCTURED_ROWS:
+        return C <= 512
+    return True
 
 
 @pytest.mark.parametrize("kname,kernel", STRUCT_KERNELS)
 @pytest.mark.parametrize("name,f", FIELDS)
 def test_structured_parity(dev, orc, name, f, kname, kernel):
     P = problem(orc, f)
+    if not kernel_fits(kernel, P.C):
+        pytest.skip("field too large for this kernel")
     R, S = (32, 300) if P.C <= 40 else (8, 60)
     h = qpath.qp_build_qubo(f)
     ref = orc.anneal_structured(P, R, S, seed=7)
@@ -112,6 +123,8 @@ def test_structured_multichunk(dev, orc, kname, kernel):
     memory here."""
     f = inputs.obstacles(18, 18, 0.1, seed=8, start=5)
     P = problem(orc, f)
+    if not kernel_fits(kernel, P.C):
+        pytest.skip("field too large for this kernel")
     assert 256 < P.C <= 512
     h = qpath.qp_build_qubo(f)
     ref = orc.anneal_structured(P, 3, 12, seed=3)
@@ -152,7 +165,7 @@ def test_structured_hot_start(dev, orc, kname, kernel):
 
 
 @pytest.mark.parametrize("kname,kernel", STRUCT_KERNELS)
-def test_structured_int32_distances(dev, orc, kname, kernel):
+def test_structured_int32_distances(dev, orc, kname, kernel):  # 23 cells: every kernel fits
     """scale = 10000 forces int32 distances while the dE bound still fits."""
     f = inputs.obstacles(5, 5, 0.1, seed=4)
     P = orc.Problem(f.rows, f.cols, f.free_mask, f.start, scale=10000)
@@ -217,7 +230,8 @@ def test_dense_path_parity_4x4_full_workload(dev, orc):
 def test_dense_equals_structured_kernels(dev, orc, name, f):
     h = qpath.qp_build_qubo(f, flags=qpath.QP_DENSE | qpath.QP_STRUCTURED)
     a = gpu_anneal(h, 16, 200, 3, kernel=qpath.QP_KERNEL_DENSE)
-    for k in (qpath.QP_KERNEL_STRUCTURED, qpath.QP_KERNEL_STRUCTURED_FLAT):
+    for k in (qpath.QP_KERNEL_STRUCTURED, qpath.QP_KERNEL_STRUCTURED_ROWS, qpath.QP_KERNEL_STRUCTURED_FLAT,
+              qpath.QP_KERNEL_STRUCTURED_GROUP):
         b = gpu_anneal(h, 16, 200, 3, kernel=k)
         for x, y in zip(a, b):
             assert (x == y).all()
@@ -358,3 +372,15 @@ def test_full_size_24x24_structured_sampled(dev, orc):
     idx = [0, 4095]
     ref = orc.anneal_structured(P, idx, w["n_sweeps"], seed=w["seed"])
     assert_same(got, ref, idx)
+
+
+@pytest.mark.parametrize("shape,p,seed,R", [((8, 8), 0.0, 1, 7), ((7, 9), 0.1, 2, 13), ((11, 11), 0.05, 3, 9),
+                                           ((2, 3), 0.0, 4, 5)])
+def test_grouped_kernel_partial_warps(dev, orc, shape, p, seed, R):
+    """Group sizes 4 (C <= 64) and 2 (C <= 128) with replica counts that leave
+    idle groups in the last warp."""
+    f = inputs.obstacles(*shape, p, seed=seed)
+    P = problem(orc, f)
+    h = qpath.qp_build_qubo(f)
+    ref = orc.anneal_structured(P, R, 120, seed=seed)
+    assert_same(gpu_anneal(h, R, 120, seed, kernel=qpath.QP_KERNEL_STRUCTURED_GROUP), ref)
