@@ -233,6 +233,108 @@ qp_status qp_decode_path(const qp_handle *h, const uint8_t *state, int32_t *path
 qp_status qp_decode_batch(const qp_handle *h, int32_t replicas, const uint8_t *states,
                           int32_t *paths_out, int64_t *lengths_out, void *cuda_stream);
 
+/* Repair R states into flight paths on the device (one warp per state), so
+ * that every state yields the feasible path the reconstruction step of
+ * Algorithm 1 hands back, then shorten each path by 2-opt.  The paper does
+ * not say how an infeasible sample is turned into a path; this is the rule:
+ *   Greedy fix.  path[0] = s; for t = 1 .. C-1 the candidates are the cells
+ *     not yet on the path with x_{t,i} = 1, or every cell not yet on the path
+ *     if there is none; path[t] = the candidate nearest to path[t-1] (smallest
+ *     d, ties to the smaller id).  A feasible state (every row and column sum
+ *     1, x_{0,s} = 1) gives exactly its decoded path.
+ *   2-opt.  Move (i, j), 1 <= i < j <= C-1, reverses path[i..j].  A pass
+ *     scans i = 1 .. C-2 and, for each, j = i+1 .. C-1 in order, applying a
+ *     move as soon as it makes the path strictly shorter and going on with
+ *     the next j on the changed path.  Passes repeat while the previous one
+ *     moved, at most max_passes of them (0: no 2-opt; < 0: until no move
+ *     helps, which always ends since each move shortens an integer length).
+ * states: R*n bytes (host or device).  paths_out: R*C int32; lengths_out: R
+ * int64 (sum of d along the path); status_out: R int32 (NULL allowed):
+ * 0 = feasible and kept as decoded, 1 = feasible and shortened by 2-opt,
+ * 2 = infeasible, repaired.  Outputs host or device; asynchronous on
+ * cuda_stream when every pointer is device memory.  QP_EINVAL for a generic
+ * QUBO. */
+qp_status qp_repair_batch(const qp_handle *h, int32_t replicas, const uint8_t *states, int32_t max_passes,
+                          int32_t *paths_out, int64_t *lengths_out, int32_t *status_out, void *cuda_stream);
+
+/* qp_repair_batch for one state (host or device) into host outputs. */
+qp_status qp_repair_path(const qp_handle *h, const uint8_t *state, int32_t max_passes, int32_t *path_out,
+                         int64_t *length_out, int32_t *status_out);
+
+/* The sampler under a wall-clock budget: the solver time limit L of
+ * Algorithm 1 (100 ms in the paper's evaluation, Section IV-C).  Runs the
+ * geometric schedule (n_sweeps, T0, T1; sweep_begin/sweep_end are ignored)
+ * on `replicas` chains, repairs every final state (qp_repair_batch with
+ * max_passes) and returns the shortest path.
+ *   Probes first run 9 sweeps of `replicas` chains at the constant
+ *   temperature T0, then 9 at T1 from the first probe's states, and time
+ *   sweeps 1..8 of each; the time per sweep is taken as the mean of the hot
+ *   (slowest) and cold (fastest) rates, and the probes' chains are
+ *   discarded.  If n_sweeps sweeps at that rate fit in what is left,
+ *   every round runs the whole schedule; otherwise a shorter schedule with the
+ *   same T0, T1 and n' sweeps runs instead, n' = the budget's share of sweeps
+ *   rounded down to m*2^e (8 <= m < 16) so that such schedules repeat and
+ *   their threshold tables are reused.  Round k anneals fresh chains with
+ *   replica indices k*R .. k*R+R-1; a round starts while the previous round's
+ *   duration still fits in the budget (round 0 always runs).
+ * Given info->n_sweeps and info->rounds the result is reproducible: it equals
+ * qp_anneal_ex over sweeps [0, n_sweeps) with replica_offset k*R for each
+ * round k, qp_repair_batch of each round's states, and the shortest path
+ * (ties to the smaller replica index).  The budget is a target, not a bound:
+ * round 0 always completes, and the first call on a schedule also builds its
+ * threshold tables on the host (inside round 0).  path_out: C int32 (host);
+ * *length_out: its length; state_out: n bytes of the winning replica's final
+ * state (host, NULL allowed); info (NULL allowed) as below.  Synchronous. */
+typedef struct {
+  int32_t n_sweeps;    /* sweeps of the schedule that ran in every round */
+  int32_t rounds;      /* rounds of `replicas` chains */
+  int32_t replica;     /* replica index of the returned path */
+  int32_t status;      /* its repair status (0, 1, 2 as in qp_repair_batch) */
+  int64_t n_feasible;  /* final states over all rounds that were feasible */
+  int64_t energy;      /* final energy E of the returned replica's state */
+  double probe_ms;     /* wall time up to the end of the probe */
+  double elapsed_ms;   /* wall time of the whole call */
+} qp_timed_info;
+qp_status qp_anneal_timed(qp_handle *h, int32_t replicas, const qp_schedule *sched, uint64_t seed,
+                          double time_limit_ms, int32_t max_passes, int32_t *path_out, int64_t *length_out,
+                          uint8_t *state_out, qp_timed_info *info, void *cuda_stream);
+
+/* Replica exchange (parallel tempering) over the replica batch.  The paper
+ * runs many chains of its sampler in parallel (Sections III-C, IV-A) and
+ * does not say whether they interact; this is the standard way to let them.
+ * G groups of M chains; chain r = g*M + m starts at level m of the ladder
+ * T_m = T_lo (T_hi/T_lo)^(m/(M-1)) (m = 0 coldest; the geometric schedule
+ * formula over M "sweeps").  Round e = 0 .. exchanges-1: every chain runs
+ * sweeps [e*I, (e+1)*I) (I = sweeps_per_exchange; the sweep index feeds the
+ * random counters as in qp_anneal) at the fixed temperature of its level,
+ * then the pairs of levels (m, m+1), m = e mod 2, m+2, ..., of every group
+ * try to trade: with a the chain at m and b the chain at m+1 and
+ * X = E_b - E_a, the trade is accepted iff X <= 0 or (X < len and
+ * u < thr[X]), thr = the threshold table at the effective temperature
+ * T_m T_{m+1} / (T_{m+1} - T_m) (so the probability is
+ * min(1, exp((1/T_m - 1/T_{m+1})(E_a - E_b)))), u = word 0 of
+ * Philox4x32-10 at counter (m, e, g, 0x50545843).  A trade swaps the two
+ * chains' levels; states stay with their chains.
+ * init_states: G*M*n bytes or NULL (all-zero start).  Outputs (host or
+ * device): states_out G*M*n final states and energies_out G*M final E, by
+ * chain; best_out G*M (NULL allowed) the best feasible E of each chain at
+ * any sweep end; levels_out G*M int32 (NULL allowed) each chain's final
+ * level; swaps_out G*(M-1) int64 (NULL allowed) accepted trades of each
+ * pair of levels.  Fields of up to 512 cells use the row kernel, larger ones
+ * the flat kernel.  Asynchronous on cuda_stream when every output is device
+ * memory; calls on one handle must not overlap (they share its buffers).
+ * QP_ERANGE if two levels are so close that the exchange temperature
+ * exceeds 1e8. */
+typedef struct {
+  int32_t levels;              /* M >= 2 */
+  double T_lo, T_hi;           /* 0 < T_lo < T_hi */
+  int32_t sweeps_per_exchange; /* I >= 1 */
+  int32_t exchanges;           /* rounds >= 1; I * rounds sweeps in all */
+} qp_pt_schedule;
+qp_status qp_anneal_pt(qp_handle *h, int32_t groups, const qp_pt_schedule *pt, uint64_t seed,
+                       const uint8_t *init_states, uint8_t *states_out, int64_t *energies_out,
+                       int64_t *best_out, int32_t *levels_out, int64_t *swaps_out, void *cuda_stream);
+
 /* ---- Learned warm start (no counterpart in the paper: a seed generator for
  * the sampler).  A per-cell MLP maps 16 features of a free cell to logits over
  * its step t in the flight path (t < 256): Linear(16,256)+ReLU,

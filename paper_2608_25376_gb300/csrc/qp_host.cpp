@@ -9,10 +9,12 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <chrono>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -160,18 +162,43 @@ qp_status device_schedule(const qp_schedule &sc, DeviceSchedule *out) {
   std::vector<int64_t> off(sc.n_sweeps);
   std::vector<int32_t> len(sc.n_sweeps);
   std::vector<float> cf(sc.n_sweeps);
-  std::vector<uint32_t> all, tab;
   const double log2e = 1.0 / std::log(2.0);
-  int32_t max_len = 0;
-  for (int s = 0; s < sc.n_sweeps; ++s) {
-    const double T = temperature(sc, s);
-    build_thresholds(T, tab);
-    cf[s] = (float)(log2e / T);
-    off[s] = (int64_t)all.size();
-    len[s] = (int32_t)tab.size();
-    max_len = std::max(max_len, len[s]);
-    all.insert(all.end(), tab.begin(), tab.end());
+  // The tables of long hot schedules run to tens of MB; host threads build
+  // contiguous sweep ranges (every entry is computed the same way whatever
+  // the split), then the ranges are placed one after another.
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int parts = std::max(1, std::min({hw, 16, sc.n_sweeps / 32 + 1}));
+  std::vector<std::vector<uint32_t>> chunk(parts);
+  auto work = [&](int p) {
+    const int s0 = (int)((int64_t)sc.n_sweeps * p / parts), s1 = (int)((int64_t)sc.n_sweeps * (p + 1) / parts);
+    std::vector<uint32_t> tab;
+    for (int s = s0; s < s1; ++s) {
+      const double T = temperature(sc, s);
+      build_thresholds(T, tab);
+      cf[s] = (float)(log2e / T);
+      off[s] = (int64_t)chunk[p].size();  // local; made global below
+      len[s] = (int32_t)tab.size();
+      chunk[p].insert(chunk[p].end(), tab.begin(), tab.end());
+    }
+  };
+  {
+    std::vector<std::thread> pool;
+    for (int p = 1; p < parts; ++p) pool.emplace_back(work, p);
+    work(0);
+    for (auto &t : pool) t.join();
   }
+  std::vector<uint32_t> all;
+  size_t total = 0;
+  for (auto &c : chunk) total += c.size();
+  all.reserve(total);
+  for (int p = 0; p < parts; ++p) {
+    const int s0 = (int)((int64_t)sc.n_sweeps * p / parts), s1 = (int)((int64_t)sc.n_sweeps * (p + 1) / parts);
+    for (int s = s0; s < s1; ++s) off[s] += (int64_t)all.size();
+    all.insert(all.end(), chunk[p].begin(), chunk[p].end());
+    std::vector<uint32_t>().swap(chunk[p]);
+  }
+  int32_t max_len = 0;
+  for (int s = 0; s < sc.n_sweeps; ++s) max_len = std::max(max_len, len[s]);
   QP_TRY(e->thr.ensure(all.size() * 4));
   QP_TRY(e->off.ensure(off.size() * 8));
   QP_TRY(e->len.ensure(len.size() * 4));
@@ -212,7 +239,9 @@ struct qp_handle {
   DevBuf frozen_bits, fval_bits;
   std::vector<uint8_t> frozen_host, fval_host;  // generic QUBOs
   // scratch
-  DevBuf gstate, hbuf, in_stage, st_stage, e_stage, b_stage, a_stage, p_stage, l_stage;
+  DevBuf gstate, hbuf, in_stage, st_stage, e_stage, b_stage, a_stage, p_stage, l_stage, r_stage;
+  DevBuf t_states[2], t_E, t_paths, t_len, t_stat;  // qp_anneal_timed
+  DevBuf pt_states[2], pt_E, pt_bseg, pt_best, pt_level, pt_owner, pt_swaps;  // qp_anneal_pt
 };
 
 namespace {
@@ -431,6 +460,34 @@ extern "C" qp_status qp_thresholds(const qp_schedule *sc, int32_t sweep, uint32_
 }
 
 // --------------------------------------------------------------------------- anneal
+namespace {
+
+// The structured sweep of a.R replicas: the row kernel when allowed and the
+// field fits it, else the flat kernel (spins in global memory when a
+// replica's bitset does not fit shared memory comfortably).
+qp_status launch_structured_auto(qp_handle *h, StructArgs &a, int W, bool allow_rows, cudaStream_t st,
+                                 LaunchInfo *info) {
+  if (allow_rows) {
+    int Wr = W;
+    while (Wr > 1 && !rows_supported(h->C, h->d_i16, Wr)) --Wr;
+    if (rows_supported(h->C, h->d_i16, Wr)) {
+      QP_CU(launch_rows(a, h->d_i16, Wr, st, info));
+      return QP_OK;
+    }
+  }
+  a.nw_pad = (int32_t)structured_gstate_words(h->C);
+  const bool want_smem = structured_state_fits_smem(h->C, h->d_i16, W) &&
+                         4 * structured_gstate_words(h->C) <= 8 * 1024;
+  if (!want_smem) {
+    QP_TRY(h->gstate.ensure((size_t)a.R * a.nw_pad * 4));
+    a.gstate = h->gstate.as<uint32_t>();
+  }
+  QP_CU(launch_structured(a, h->d_i16, W, want_smem, st, info));
+  return QP_OK;
+}
+
+}  // namespace
+
 extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc, uint64_t seed,
                                   const uint8_t *init, uint8_t *states_out, int64_t *energies_out,
                                   int64_t *best_out, const qp_anneal_opts *opts, void *stream_) {
@@ -497,22 +554,7 @@ extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc
       QP_CU(launch_group(a, h->d_i16, Wg, st, &info));
       goto launched;
     }
-    if (kernel == QP_KERNEL_STRUCTURED || kernel == QP_KERNEL_STRUCTURED_ROWS) {
-      int Wr = W;
-      while (Wr > 1 && !rows_supported(h->C, h->d_i16, Wr)) --Wr;
-      if (rows_supported(h->C, h->d_i16, Wr)) {
-        QP_CU(launch_rows(a, h->d_i16, Wr, st, &info));
-        goto launched;
-      }
-    }
-    a.nw_pad = (int32_t)structured_gstate_words(h->C);
-    const bool want_smem = structured_state_fits_smem(h->C, h->d_i16, W) &&
-                           4 * structured_gstate_words(h->C) <= 8 * 1024;
-    if (!want_smem) {
-      QP_TRY(h->gstate.ensure((size_t)R * a.nw_pad * 4));
-      a.gstate = h->gstate.as<uint32_t>();
-    }
-    QP_CU(launch_structured(a, h->d_i16, W, want_smem, st, &info));
+    QP_TRY(launch_structured_auto(h, a, W, kernel != QP_KERNEL_STRUCTURED_FLAT, st, &info));
   } else {
     int W = o.replicas_per_cta ? o.replicas_per_cta : 4;
     while (W > 1 && !dense_h_fits_smem(h->n, h->path ? h->C : 0, W)) --W;
@@ -543,6 +585,152 @@ extern "C" qp_status qp_anneal(qp_handle *h, int32_t R, const qp_schedule *sc, u
                                const uint8_t *init, uint8_t *states_out, int64_t *energies_out,
                                int64_t *best_out, void *stream) {
   return qp_anneal_ex(h, R, sc, seed, init, states_out, energies_out, best_out, nullptr, stream);
+}
+
+// --------------------------------------------------------------------------- replica exchange
+namespace {
+
+struct XchgEntry {
+  DevBuf thr, off, len;
+};
+std::mutex g_xchg_mu;
+std::map<SchedKey, std::unique_ptr<XchgEntry>> g_xchg;
+
+// Exchange tables of a ladder: row m (m < M-1) holds the Metropolis
+// thresholds at T_m T_{m+1} / (T_{m+1} - T_m); built once per device.
+qp_status exchange_tables(const qp_schedule &ladder, const uint32_t **thr, const int64_t **off,
+                          const int32_t **len) {
+  int dev = 0;
+  QP_CU(cudaGetDevice(&dev));
+  SchedKey key{dev, ladder.n_sweeps, 0, 0};
+  std::memcpy(&key.t0, &ladder.T0, 8);
+  std::memcpy(&key.t1, &ladder.T1, 8);
+  std::lock_guard<std::mutex> lk(g_xchg_mu);
+  auto it = g_xchg.find(key);
+  if (it == g_xchg.end()) {
+    const int M = ladder.n_sweeps;
+    std::vector<int64_t> o(M - 1);
+    std::vector<int32_t> l(M - 1);
+    std::vector<uint32_t> all, tab;
+    for (int m = 0; m + 1 < M; ++m) {
+      const double Tm = temperature(ladder, m), Tn = temperature(ladder, m + 1);
+      const double Te = Tm * Tn / (Tn - Tm);
+      if (!(Te > 0.0) || !std::isfinite(Te) || Te > 1e8)
+        return fail(QP_ERANGE, "ladder levels %d and %d are too close (exchange temperature %g)", m, m + 1, Te);
+      build_thresholds(Te, tab);
+      o[m] = (int64_t)all.size();
+      l[m] = (int32_t)tab.size();
+      all.insert(all.end(), tab.begin(), tab.end());
+    }
+    auto e = std::make_unique<XchgEntry>();
+    QP_TRY(e->thr.ensure(all.size() * 4));
+    QP_TRY(e->off.ensure(o.size() * 8));
+    QP_TRY(e->len.ensure(l.size() * 4));
+    QP_CU(cudaMemcpy(e->thr.p, all.data(), all.size() * 4, cudaMemcpyHostToDevice));
+    QP_CU(cudaMemcpy(e->off.p, o.data(), o.size() * 8, cudaMemcpyHostToDevice));
+    QP_CU(cudaMemcpy(e->len.p, l.data(), l.size() * 4, cudaMemcpyHostToDevice));
+    it = g_xchg.emplace(key, std::move(e)).first;
+  }
+  *thr = it->second->thr.as<uint32_t>();
+  *off = it->second->off.as<int64_t>();
+  *len = it->second->len.as<int32_t>();
+  return QP_OK;
+}
+
+}  // namespace
+
+extern "C" qp_status qp_anneal_pt(qp_handle *h, int32_t G, const qp_pt_schedule *pt, uint64_t seed,
+                                  const uint8_t *init, uint8_t *states_out, int64_t *energies_out,
+                                  int64_t *best_out, int32_t *levels_out, int64_t *swaps_out, void *stream_) {
+  g_err.clear();
+  if (!h || !pt || !states_out || !energies_out || G < 1) return fail(QP_EINVAL, "bad argument");
+  if (!h->path) return fail(QP_EINVAL, "replica exchange needs a handle built by qp_build_qubo");
+  const int M = pt->levels, I = pt->sweeps_per_exchange, X = pt->exchanges;
+  if (M < 2 || I < 1 || X < 1) return fail(QP_EINVAL, "need levels >= 2, sweeps_per_exchange >= 1, exchanges >= 1");
+  if (!(pt->T_lo > 0.0) || !(pt->T_hi > pt->T_lo) || !std::isfinite(pt->T_hi))
+    return fail(QP_EINVAL, "need 0 < T_lo < T_hi (finite)");
+  if ((int64_t)G * M > INT32_MAX / 2) return fail(QP_ERANGE, "too many chains");
+  if ((int64_t)I * X > INT32_MAX) return fail(QP_ERANGE, "too many sweeps");
+  qp_schedule ladder{M, pt->T_lo, pt->T_hi, 0, M};
+  QP_TRY(check_schedule(&ladder));
+  const int32_t R = G * M;
+  DevSet ds(h->dev);
+  cudaStream_t st = static_cast<cudaStream_t>(stream_);
+  DeviceSchedule lt;
+  QP_TRY(device_schedule(ladder, &lt));
+  const uint32_t *xthr;
+  const int64_t *xoff;
+  const int32_t *xlen;
+  QP_TRY(exchange_tables(ladder, &xthr, &xoff, &xlen));
+  const size_t n = (size_t)h->n;
+  QP_TRY(h->pt_states[0].ensure((size_t)R * n));
+  QP_TRY(h->pt_states[1].ensure((size_t)R * n));
+  QP_TRY(h->pt_E.ensure((size_t)R * 8));
+  QP_TRY(h->pt_bseg.ensure((size_t)R * 8));
+  QP_TRY(h->pt_best.ensure((size_t)R * 8));
+  QP_TRY(h->pt_level.ensure((size_t)R * 4));
+  QP_TRY(h->pt_owner.ensure((size_t)R * 4));
+  QP_TRY(h->pt_swaps.ensure((size_t)G * (M - 1) * 8));
+  {
+    std::vector<int32_t> lev(R), own(R);
+    std::vector<int64_t> best(R, INT64_MAX);
+    for (int r = 0; r < R; ++r) {
+      lev[r] = r % M;
+      own[r] = r;
+    }
+    QP_CU(cudaMemcpyAsync(h->pt_level.p, lev.data(), (size_t)R * 4, cudaMemcpyHostToDevice, st));
+    QP_CU(cudaMemcpyAsync(h->pt_owner.p, own.data(), (size_t)R * 4, cudaMemcpyHostToDevice, st));
+    QP_CU(cudaMemcpyAsync(h->pt_best.p, best.data(), (size_t)R * 8, cudaMemcpyHostToDevice, st));
+    QP_CU(cudaMemsetAsync(h->pt_swaps.p, 0, (size_t)G * (M - 1) * 8, st));
+    QP_CU(cudaStreamSynchronize(st));  // the host vectors go out of scope
+  }
+  const uint8_t *init_d = init;
+  if (init && !is_device_ptr(init)) {
+    QP_TRY(h->in_stage.ensure((size_t)R * n));
+    QP_CU(cudaMemcpyAsync(h->in_stage.p, init, (size_t)R * n, cudaMemcpyHostToDevice, st));
+    init_d = h->in_stage.as<uint8_t>();
+  }
+  uint8_t *cur = h->pt_states[0].as<uint8_t>(), *nxt = h->pt_states[1].as<uint8_t>();
+  StructArgs a{};
+  a.C = h->C; a.Cp = h->Cp; a.start = h->start; a.A = h->A; a.B = h->B;
+  a.d = h->d_dev.p;
+  a.R = R; a.rep_offset = 0;
+  a.key0 = (uint32_t)seed; a.key1 = (uint32_t)(seed >> 32);
+  a.thr = lt.thr; a.thr_off = lt.off; a.thr_len = lt.len; a.thr_c = lt.c;
+  a.E_out = h->pt_E.as<int64_t>(); a.best_out = h->pt_bseg.as<int64_t>(); a.acc_out = nullptr;
+  a.level = h->pt_level.as<int32_t>();
+  PtArgs x{};
+  x.G = G; x.M = M;
+  x.E = h->pt_E.as<int64_t>(); x.best_seg = h->pt_bseg.as<int64_t>(); x.best = h->pt_best.as<int64_t>();
+  x.owner = h->pt_owner.as<int32_t>(); x.level = h->pt_level.as<int32_t>(); x.swaps = h->pt_swaps.as<int64_t>();
+  x.thr = xthr; x.off = xoff; x.len = xlen;
+  x.key0 = a.key0; x.key1 = a.key1;
+  LaunchInfo info;
+  for (int e = 0; e < X; ++e) {
+    a.sweep_begin = e * I;
+    a.sweep_end = (e + 1) * I;
+    a.init = e == 0 ? init_d : cur;
+    a.states_out = nxt;
+    QP_TRY(launch_structured_auto(h, a, 4, true, st, &info));
+    x.phase = e & 1;
+    x.round = e;
+    QP_CU(launch_pt_exchange(x, st));
+    std::swap(cur, nxt);
+  }
+  bool host_out = false;
+  auto put = [&](void *dst, const void *src, size_t bytes) -> qp_status {
+    if (!dst) return QP_OK;
+    host_out = host_out || !is_device_ptr(dst);
+    QP_CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+    return QP_OK;
+  };
+  QP_TRY(put(states_out, cur, (size_t)R * n));
+  QP_TRY(put(energies_out, h->pt_E.p, (size_t)R * 8));
+  QP_TRY(put(best_out, h->pt_best.p, (size_t)R * 8));
+  QP_TRY(put(levels_out, h->pt_level.p, (size_t)R * 4));
+  QP_TRY(put(swaps_out, h->pt_swaps.p, (size_t)G * (M - 1) * 8));
+  if (host_out || (init && init_d != init)) QP_CU(cudaStreamSynchronize(st));
+  return QP_OK;
 }
 
 // --------------------------------------------------------------------------- decode
@@ -606,6 +794,197 @@ extern "C" qp_status qp_decode_batch(const qp_handle *hc, int32_t R, const uint8
   if (ph) QP_CU(cudaMemcpyAsync(paths_out, pd, (size_t)R * h->C * 4, cudaMemcpyDeviceToHost, st));
   if (lh) QP_CU(cudaMemcpyAsync(lengths_out, ld, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
   if (sync || ph || lh) QP_CU(cudaStreamSynchronize(st));
+  return QP_OK;
+}
+
+extern "C" qp_status qp_repair_batch(const qp_handle *hc, int32_t R, const uint8_t *states, int32_t max_passes,
+                                     int32_t *paths_out, int64_t *lengths_out, int32_t *status_out,
+                                     void *stream_) {
+  g_err.clear();
+  qp_handle *h = const_cast<qp_handle *>(hc);
+  if (!h || !states || !paths_out || !lengths_out || R < 1) return fail(QP_EINVAL, "bad argument");
+  if (!h->path) return fail(QP_EINVAL, "a generic QUBO has no path");
+  DevSet ds(h->dev);
+  cudaStream_t st = static_cast<cudaStream_t>(stream_);
+  const size_t n = (size_t)h->n;
+  const uint8_t *sd = states;
+  bool sync = false;
+  if (!is_device_ptr(states)) {
+    QP_TRY(h->in_stage.ensure((size_t)R * n));
+    QP_CU(cudaMemcpyAsync(h->in_stage.p, states, (size_t)R * n, cudaMemcpyHostToDevice, st));
+    sd = h->in_stage.as<uint8_t>();
+    sync = true;
+  }
+  int32_t *pd = paths_out, *rd = status_out;
+  int64_t *ld = lengths_out;
+  const bool ph = !is_device_ptr(paths_out), lh = !is_device_ptr(lengths_out);
+  const bool rh = status_out && !is_device_ptr(status_out);
+  if (ph) { QP_TRY(h->p_stage.ensure((size_t)R * h->C * 4)); pd = h->p_stage.as<int32_t>(); }
+  if (lh) { QP_TRY(h->l_stage.ensure((size_t)R * 8)); ld = h->l_stage.as<int64_t>(); }
+  if (!status_out || rh) { QP_TRY(h->r_stage.ensure((size_t)R * 4)); rd = h->r_stage.as<int32_t>(); }
+  QP_CU(launch_repair(sd, R, h->C, h->start, h->d32_dev.as<int32_t>(), max_passes, pd, ld, rd, st));
+  if (ph) QP_CU(cudaMemcpyAsync(paths_out, pd, (size_t)R * h->C * 4, cudaMemcpyDeviceToHost, st));
+  if (lh) QP_CU(cudaMemcpyAsync(lengths_out, ld, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
+  if (rh) QP_CU(cudaMemcpyAsync(status_out, rd, (size_t)R * 4, cudaMemcpyDeviceToHost, st));
+  if (sync || ph || lh || rh) QP_CU(cudaStreamSynchronize(st));
+  return QP_OK;
+}
+
+extern "C" qp_status qp_repair_path(const qp_handle *h, const uint8_t *state, int32_t max_passes,
+                                    int32_t *path_out, int64_t *length_out, int32_t *status_out) {
+  if (!path_out || !length_out || is_device_ptr(path_out) || is_device_ptr(length_out) ||
+      (status_out && is_device_ptr(status_out)))
+    return fail(QP_EINVAL, "qp_repair_path: outputs must be host memory");
+  int32_t status = 0;
+  QP_TRY(qp_repair_batch(h, 1, state, max_passes, path_out, length_out, &status, nullptr));
+  if (status_out) *status_out = status;
+  return QP_OK;
+}
+
+namespace {
+
+double ms_since(const std::chrono::steady_clock::time_point &t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// n rounded down to m * 2^e with 8 <= m < 16 (n itself below 16), so that
+// budget-fitted schedules come from a short list and their tables are reused.
+int32_t quantize_sweeps(int64_t n) {
+  if (n < 16) return (int32_t)std::max<int64_t>(1, n);
+  int e = 0;
+  while ((n >> e) >= 16) ++e;
+  return (int32_t)((n >> e) << e);
+}
+
+}  // namespace
+
+extern "C" qp_status qp_anneal_timed(qp_handle *h, int32_t R, const qp_schedule *sc, uint64_t seed,
+                                     double time_limit_ms, int32_t max_passes, int32_t *path_out,
+                                     int64_t *length_out, uint8_t *state_out, qp_timed_info *info,
+                                     void *stream_) {
+  const auto t0 = std::chrono::steady_clock::now();
+  g_err.clear();
+  if (!h || !sc || !path_out || !length_out || R < 1) return fail(QP_EINVAL, "bad argument");
+  if (!h->path) return fail(QP_EINVAL, "qp_anneal_timed needs a handle built by qp_build_qubo");
+  if (!(time_limit_ms > 0.0) || !std::isfinite(time_limit_ms)) return fail(QP_EINVAL, "time_limit_ms must be > 0");
+  qp_schedule full = *sc;
+  full.sweep_begin = 0;
+  full.sweep_end = full.n_sweeps;
+  QP_TRY(check_schedule(&full));
+  if ((int64_t)R * 2 > INT32_MAX) return fail(QP_ERANGE, "too many replicas");
+  DevSet ds(h->dev);
+  cudaStream_t st = static_cast<cudaStream_t>(stream_);
+  const size_t n = (size_t)h->n;
+  const int C = h->C;
+  QP_TRY(h->t_states[0].ensure((size_t)R * n));
+  QP_TRY(h->t_states[1].ensure((size_t)R * n));
+  QP_TRY(h->t_E.ensure((size_t)R * 8));
+  QP_TRY(h->t_paths.ensure((size_t)R * C * 4));
+  QP_TRY(h->t_len.ensure((size_t)R * 8));
+  QP_TRY(h->t_stat.ensure((size_t)R * 4));
+  uint8_t *S0 = h->t_states[0].as<uint8_t>(), *S1 = h->t_states[1].as<uint8_t>();
+  int64_t *E = h->t_E.as<int64_t>(), *Ld = h->t_len.as<int64_t>();
+  int32_t *Pd = h->t_paths.as<int32_t>(), *Sd = h->t_stat.as<int32_t>();
+  DeviceSchedule dsched;
+  QP_TRY(device_schedule(full, &dsched));
+
+  std::vector<int64_t> len(R), en(R);
+  std::vector<int32_t> stat(R);
+  struct Best {
+    int64_t length = INT64_MAX, energy = 0;
+    int32_t replica = -1, status = 0;
+  } best;
+  int64_t n_feasible = 0;
+  // Repair the R final states in `S`, fold them into `best` (shortest path,
+  // ties to the smaller replica index) and keep the winner's path and state.
+  auto harvest = [&](const uint8_t *S, int32_t offset) -> qp_status {
+    QP_CU(launch_repair(S, R, C, h->start, h->d32_dev.as<int32_t>(), max_passes, Pd, Ld, Sd, st));
+    QP_CU(cudaMemcpyAsync(len.data(), Ld, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
+    QP_CU(cudaMemcpyAsync(stat.data(), Sd, (size_t)R * 4, cudaMemcpyDeviceToHost, st));
+    QP_CU(cudaMemcpyAsync(en.data(), E, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
+    QP_CU(cudaStreamSynchronize(st));
+    int arg = -1;
+    for (int r = 0; r < R; ++r) {
+      n_feasible += stat[r] != 2;
+      if (len[r] < best.length) {
+        best.length = len[r];
+        arg = r;
+      }
+    }
+    if (arg >= 0) {
+      best.replica = offset + arg;
+      best.status = stat[arg];
+      best.energy = en[arg];
+      QP_CU(cudaMemcpyAsync(path_out, Pd + (size_t)arg * C, (size_t)C * 4, cudaMemcpyDeviceToHost, st));
+      if (state_out) QP_CU(cudaMemcpyAsync(state_out, S + (size_t)arg * n, n, cudaMemcpyDeviceToHost, st));
+      QP_CU(cudaStreamSynchronize(st));
+    }
+    return QP_OK;
+  };
+  auto run = [&](const qp_schedule &s, int32_t b, int32_t e, const uint8_t *init, uint8_t *out,
+                 int32_t offset) -> qp_status {
+    qp_schedule part = s;
+    part.sweep_begin = b;
+    part.sweep_end = e;
+    qp_anneal_opts o{};
+    o.replica_offset = offset;
+    return qp_anneal_ex(h, R, &part, seed, init, out, E, nullptr, &o, st);
+  };
+
+  // Probes: 9 sweeps at the constant temperature T0, then 9 at T1 starting
+  // from the first probe's states; sweeps 1..8 of each are timed (sweep 0 of
+  // the first also pays any first-launch cost).  Hot sweeps are the slowest
+  // and cold ones the fastest; the schedule's time per sweep is taken as the
+  // mean of the two.  The probes' chains are thrown away; their tables are 9
+  // short rows each.
+  auto probe_at = [&](double T, const uint8_t *init, uint8_t *out, double *ms_out) -> qp_status {
+    qp_schedule pr = full;
+    pr.n_sweeps = 9;
+    pr.T0 = pr.T1 = T;
+    pr.sweep_end = 9;
+    QP_TRY(run(pr, 0, 1, init, S1, 0));
+    QP_CU(cudaStreamSynchronize(st));
+    const double ta = ms_since(t0);
+    QP_TRY(run(pr, 1, 9, S1, out, 0));
+    QP_CU(cudaStreamSynchronize(st));
+    *ms_out = (ms_since(t0) - ta) / 8.0;
+    return QP_OK;
+  };
+  double t_hot = 0.0, t_cold = 0.0;
+  QP_TRY(probe_at(full.T0, nullptr, S0, &t_hot));
+  QP_TRY(probe_at(full.T1, S0, S0, &t_cold));
+  const double probe_ms = ms_since(t0);
+  const double per_sweep = std::max(0.5 * (t_hot + t_cold), 1e-6);
+  const double left = time_limit_ms - probe_ms;
+  int32_t n_used = full.n_sweeps;
+  if (per_sweep * full.n_sweeps > 0.9 * left)  // the schedule does not fit: a shorter one that does
+    n_used = std::min(full.n_sweeps, quantize_sweeps((int64_t)std::max(1.0, 0.8 * left / per_sweep)));
+  qp_schedule used = full;
+  used.n_sweeps = n_used;
+  used.sweep_end = n_used;
+  // Rounds of fresh chains (replica indices k*R .. k*R+R-1 in round k); a
+  // round starts while the previous one's duration still fits in what is left.
+  int32_t rounds = 0;
+  double round_ms = 0.0;
+  while ((int64_t)(rounds + 1) * R <= INT32_MAX) {
+    const double now = ms_since(t0);
+    if (rounds > 0 && now + round_ms > time_limit_ms) break;
+    QP_TRY(run(used, 0, n_used, nullptr, S0, rounds * R));
+    QP_TRY(harvest(S0, rounds * R));
+    round_ms = ms_since(t0) - now;
+    ++rounds;
+  }
+  *length_out = best.length;
+  if (info) {
+    info->n_sweeps = n_used;
+    info->rounds = rounds;
+    info->replica = best.replica;
+    info->status = best.status;
+    info->n_feasible = n_feasible;
+    info->energy = best.energy;
+    info->probe_ms = probe_ms;
+    info->elapsed_ms = ms_since(t0);
+  }
   return QP_OK;
 }
 

@@ -42,6 +42,9 @@ struct StructArgs {
   int64_t *E_out, *best_out, *acc_out;  // best/acc may be null
   uint32_t *gstate;          // R x nw_pad words when the state lives in global memory
   int32_t nw_pad;
+  // Replica exchange: the table row replica r (local index) uses in every
+  // sweep of the launch (its ladder level); null = row s for sweep s.
+  const int32_t *level;
 };
 
 // Arguments of the dense sweep (one warp = one replica).
@@ -103,6 +106,28 @@ cudaError_t launch_decode(const uint8_t *states, int32_t R, int32_t C, const int
 
 // Read-only views used by the allocation-free entry point (qp_noalloc.cu);
 // none of these allocate.
+// Repair of R states into paths (greedy fix + 2-opt), one warp per replica.
+size_t repair_smem_per_warp(int32_t C);
+cudaError_t launch_repair(const uint8_t *states, int32_t R, int32_t C, int32_t start, const int32_t *d32,
+                          int32_t max_passes, int32_t *paths, int64_t *lengths, int32_t *status,
+                          cudaStream_t st);
+
+// Replica exchange round (qp_pt.cu).
+struct PtArgs {
+  int32_t G, M, phase, round;
+  const int64_t *E;          // R final energies of the last block of sweeps
+  const int64_t *best_seg;   // R best feasible energies of that block (null: skip the fold)
+  int64_t *best;             // R running minimum
+  int32_t *owner;            // G x M: chain at each level
+  int32_t *level;            // R: level of each chain
+  int64_t *swaps;            // G x (M-1) accepted trades per pair
+  const uint32_t *thr;       // exchange tables, row m at off[m], len[m] entries
+  const int64_t *off;
+  const int32_t *len;
+  uint32_t key0, key1;
+};
+cudaError_t launch_pt_exchange(const PtArgs &a, cudaStream_t st);
+
 struct StructView {
   int dev;
   int32_t C, Cp, start, A, B;

@@ -176,12 +176,14 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32)
   long long E = (long long)B * warp_sum64(hd) + (long long)A * warp_sum64(pen);
   viol = __reduce_add_sync(kFull, viol);
   long long best = LLONG_MAX, acc = 0;
+  const int lev = a.level ? __ldg(a.level + r) : -1;
 
   // ---- sweeps
   for (int s = a.sweep_begin; s < a.sweep_end; ++s) {
-    const uint32_t *thr = a.thr + a.thr_off[s];
-    const int len = a.thr_len[s];
-    const float cT = a.thr_c[s];
+    const int ts = lev >= 0 ? lev : s;  // table row: the sweep, or the replica's ladder level
+    const uint32_t *thr = a.thr + a.thr_off[ts];
+    const int len = a.thr_len[ts];
+    const float cT = a.thr_c[ts];
     for (int t = 1; t < C; ++t) {
       int nh = collect_hot(st, (t - 1) * C, C, hot, 0, lane);
       if (t + 1 < C) nh = collect_hot(st, (t + 1) * C, C, hot, nh, lane);

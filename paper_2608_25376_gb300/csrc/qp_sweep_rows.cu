@@ -59,12 +59,14 @@ __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_
   long long best = LLONG_MAX, acc = 0;
 
   // ---- sweeps
+  const int lev = a.level ? __ldg(a.level + r) : -1;
   for (int s = a.sweep_begin; s < a.sweep_end; ++s) {
-    const uint32_t *thr = a.thr + a.thr_off[s];
-    const int len = a.thr_len[s];
+    const int ts = lev >= 0 ? lev : s;  // table row: the sweep, or the replica's ladder level
+    const uint32_t *thr = a.thr + a.thr_off[ts];
+    const int len = a.thr_len[ts];
     const unsigned lenm1 = (unsigned)(len - 1);
     const unsigned hi = 0x80000000u - lenm1;
-    const float cT = a.thr_c[s];
+    const float cT = a.thr_c[ts];
     int P[NCH][4], Cu[NCH][4], N[NCH][4], Nn[NCH][4];
     zero<NCH>(P);
     zero<NCH>(Cu);

@@ -28,7 +28,7 @@ E_NONE = np.iinfo(np.int64).max
 SYMBOLS = ["qp_build_qubo", "qp_build_from_dense", "qp_qubo_info", "qp_export_dense", "qp_export_dist",
            "qp_thresholds", "qp_anneal", "qp_anneal_ex", "qp_anneal_noalloc", "qp_batch_create",
            "qp_batch_run", "qp_batch_info", "qp_batch_destroy", "qp_anneal_batch", "qp_decode_path",
-           "qp_decode_batch", "qp_ws_create", "qp_ws_destroy", "qp_ws_param_count", "qp_ws_get_params",
+           "qp_decode_batch", "qp_repair_batch", "qp_repair_path", "qp_anneal_timed", "qp_anneal_pt", "qp_ws_create", "qp_ws_destroy", "qp_ws_param_count", "qp_ws_get_params",
            "qp_ws_set_params", "qp_ws_features", "qp_ws_forward", "qp_ws_grads", "qp_ws_train_step",
            "qp_ws_decode", "qp_ws_decode_walk", "qp_destroy", "qp_last_error"]
 
@@ -50,6 +50,21 @@ class qp_schedule(ct.Structure):
 
 class qp_batch_opts(ct.Structure):
     _fields_ = [("replicas_per_cta", ct.c_int32), ("ctas", ct.c_int32)]
+
+
+class qp_timed_info(ct.Structure):
+    _fields_ = [("n_sweeps", ct.c_int32), ("rounds", ct.c_int32), ("replica", ct.c_int32), ("status", ct.c_int32),
+                ("n_feasible", ct.c_int64), ("energy", ct.c_int64), ("probe_ms", ct.c_double),
+                ("elapsed_ms", ct.c_double)]
+
+
+class qp_pt_schedule(ct.Structure):
+    _fields_ = [("levels", ct.c_int32), ("T_lo", ct.c_double), ("T_hi", ct.c_double),
+                ("sweeps_per_exchange", ct.c_int32), ("exchanges", ct.c_int32)]
+
+
+def pt_schedule(levels, T_lo, T_hi, sweeps_per_exchange, exchanges) -> qp_pt_schedule:
+    return qp_pt_schedule(int(levels), float(T_lo), float(T_hi), int(sweeps_per_exchange), int(exchanges))
 
 
 class qp_anneal_opts(ct.Structure):
@@ -98,6 +113,11 @@ def lib():
                 "qp_ws_decode_walk": [vp, i32, i32, i32, vp, vp, vp],
                 "qp_decode_path": [vp, vp, vp, vp],
                 "qp_decode_batch": [vp, i32, vp, vp, vp, vp],
+                "qp_repair_batch": [vp, i32, vp, i32, vp, vp, vp, vp],
+                "qp_repair_path": [vp, vp, i32, vp, P(i64), P(i32)],
+                "qp_anneal_pt": [vp, i32, P(qp_pt_schedule), u64, vp, vp, vp, vp, vp, vp, vp],
+                "qp_anneal_timed": [vp, i32, P(qp_schedule), u64, ct.c_double, i32, vp, P(i64), vp,
+                                    P(qp_timed_info), vp],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -328,6 +348,47 @@ def qp_decode_path(h: Handle, state):
 def qp_decode_batch(h: Handle, replicas, states, paths_out, lengths_out, stream=None):
     _check(lib().qp_decode_batch(h.ptr, int(replicas), _ptr(states), _ptr(paths_out), _ptr(lengths_out),
                                  _stream(stream)))
+
+
+def qp_anneal_pt(h: Handle, groups, pt, seed, init_states, states_out, energies_out, best_out=None,
+                 levels_out=None, swaps_out=None, stream=None):
+    _check(lib().qp_anneal_pt(h.ptr, int(groups), ct.byref(pt), ct.c_uint64(seed), _ptr(init_states),
+                              _ptr(states_out), _ptr(energies_out), _ptr(best_out), _ptr(levels_out),
+                              _ptr(swaps_out), _stream(stream)))
+
+
+REPAIR_KEPT, REPAIR_SHORTENED, REPAIR_FIXED = 0, 1, 2
+
+
+def qp_repair_batch(h: Handle, replicas, states, max_passes, paths_out, lengths_out, status_out=None,
+                    stream=None):
+    _check(lib().qp_repair_batch(h.ptr, int(replicas), _ptr(states), int(max_passes), _ptr(paths_out),
+                                 _ptr(lengths_out), _ptr(status_out), _stream(stream)))
+
+
+def qp_repair_path(h: Handle, state, max_passes=0):
+    """-> (path int32[C], length, status)"""
+    C = qp_qubo_info(h)["C"]
+    path = np.zeros(C, np.int32)
+    L, S = ct.c_int64(), ct.c_int32()
+    _check(lib().qp_repair_path(h.ptr, _ptr(state), int(max_passes), _ptr(path), ct.byref(L), ct.byref(S)))
+    return path, L.value, S.value
+
+
+def qp_anneal_timed(h: Handle, replicas, sched, seed, time_limit_ms, max_passes=0, want_state=False,
+                    stream=None) -> dict:
+    """-> {"path", "length", "state" (or None), and every qp_timed_info field}"""
+    info = qp_qubo_info(h)
+    path = np.zeros(info["C"], np.int32)
+    state = np.zeros(info["n"], np.uint8) if want_state else None
+    L = ct.c_int64()
+    ti = qp_timed_info()
+    _check(lib().qp_anneal_timed(h.ptr, int(replicas), ct.byref(sched), ct.c_uint64(seed), float(time_limit_ms),
+                                 int(max_passes), _ptr(path), ct.byref(L), _ptr(state), ct.byref(ti),
+                                 _stream(stream)))
+    out = {"path": path, "length": L.value, "state": state}
+    out.update({k: getattr(ti, k) for k, _ in qp_timed_info._fields_})
+    return out
 
 
 def qp_destroy(h: Handle):
