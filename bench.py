@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-warm-start", action="store_true")
     ap.add_argument("--no-paper-protocol", action="store_true")
+    ap.add_argument("--no-replica-exchange", action="store_true")
     ap.add_argument("--replicas-per-cta", type=int, default=0)
     ap.add_argument("--structured-kernel", default="rows", choices=["rows", "flat"])
     ap.add_argument("--profile-case", default=None, choices=["rows", "flat", "dense"],
@@ -277,6 +278,56 @@ def bench_warm_start():
                         f"labels+training {prep:.1f} s"}
 
 
+def bench_replica_exchange(f, flush, stream):
+    """Replica exchange on the bench field: 1024 chains as 32 groups x 32
+    ladder levels (T 2 -> 1000), 25 sweeps between exchange rounds, 200 rounds
+    (5000 sweeps per chain, as the plain anneal).  Best path found (minimum
+    best-feasible energy = length, B = 1) against the plain anneal at the same
+    sweeps and at the same wall time (plain restarts with fresh seeds)."""
+    import math
+    import torch
+    from paper_2608_25376_gb300 import qpath
+    h = qpath.qp_build_qubo(f)
+    n, C = h.info["n"], h.info["C"]
+    G, M, I, rounds = 32, 32, 25, 200
+    R = G * M
+    st = torch.zeros((R, n), dtype=torch.uint8, device="cuda")
+    E = torch.zeros(R, dtype=torch.int64, device="cuda")
+    B = torch.zeros(R, dtype=torch.int64, device="cuda")
+    lv = torch.zeros(R, dtype=torch.int32, device="cuda")
+    sw = torch.zeros(G * (M - 1), dtype=torch.int64, device="cuda")
+    pt = qpath.pt_schedule(M, 2.0, 1000.0, I, rounds)
+
+    def timed(fn):
+        flush.fill_(3)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b)
+
+    qpath.qp_anneal_pt(h, G, qpath.pt_schedule(M, 2.0, 1000.0, I, 2), 1, None, st, E, B, lv, sw, stream=stream)
+    pt_ms = timed(lambda: qpath.qp_anneal_pt(h, G, pt, 1, None, st, E, B, lv, sw, stream=stream))
+    pt_best = int(B.min().item())
+    trade = (sw.view(G, M - 1).double().mean(0) / (rounds / 2)).cpu().numpy()
+    sc = qpath.schedule(I * rounds)
+    plain = []
+    k = 0
+    spent = 0.0
+    while k < 1 or spent < pt_ms:
+        k += 1
+        spent += timed(lambda: qpath.qp_anneal(h, R, sc, k, None, st, E, B, stream=stream))
+        plain.append(int(B.min().item()))
+    attempts = R * I * rounds * (C - 1) ** 2
+    h.close()
+    return {"config": f"{G} groups x {M} levels, T 2 -> 1000 geometric, {I} sweeps per exchange, {rounds} rounds",
+            "value": attempts / (pt_ms / 1e3), "unit": UNIT, "ms": pt_ms,
+            "best_length": pt_best, "plain_best_same_sweeps": plain[0],
+            "plain_best_same_time": min(plain), "plain_restarts": k, "plain_ms": spent,
+            "trade_rate_min_max": [float(trade.min()), float(trade.max())]}
+
+
 def bench_paper_protocol():
     """The paper's evaluation protocol (Section IV-C, Table II): full M x N
     grids from a corner, the solver under a 100 ms limit.  Each grid runs the
@@ -439,6 +490,9 @@ def run_ours(args):
 
     if not args.no_batch and rank == 0:
         line.setdefault("variants", {})["batched"] = bench_batch(args, flush, stream)
+
+    if not args.no_replica_exchange and rank == 0:
+        line.setdefault("variants", {})["replica_exchange"] = bench_replica_exchange(f, flush, stream)
 
     if not args.no_warm_start and rank == 0:
         line["warm_start"] = bench_warm_start()

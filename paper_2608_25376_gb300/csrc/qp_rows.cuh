@@ -1,6 +1,7 @@
-// Device helpers of the row-parallel structured sweeps (qp_sweep_rows.cu,
-// qp_sweep_dual.cu): distance-row loads, row fields, the single-cell cache
-// and the evaluation of one row chunk.  Included inside namespace qp::{anon}.
+// Device helpers of the row-parallel structured sweep (qp_sweep_rows.cu:
+// the single-field and the batched persistent kernels): distance-row loads,
+// row fields, the single-cell cache and the evaluation of one row chunk.
+// Included inside namespace qp::{anon}.
 #pragma once
 
 __host__ __device__ constexpr size_t align16r(size_t x) { return (x + 15) & ~size_t(15); }

@@ -164,6 +164,23 @@ def test_structured_hot_start(dev, orc, kname, kernel):
     assert_same(gpu_anneal(h, R, 30, 13, T0=5e4, T1=5e4, init=init, kernel=kernel), ref)
 
 
+@pytest.mark.parametrize("T0,T1", [(24000.0, 20000.0), (26000.0, 25000.0), (1500.0, 900.0), (40.0, 3.0),
+                                   (2.0, 0.25)])
+@pytest.mark.parametrize("kname,kernel", STRUCT_KERNELS)
+def test_structured_temperature_edges(dev, orc, kname, kernel, T0, T1):
+    """Schedules around the row kernel's switch between acceptance bounds
+    (T below ~24500) and per-pass table tests (above), and very cold ones:
+    dense random starts give many accepts and many draws per row."""
+    f = inputs.obstacles(8, 9, 0.1, seed=21, start=5)
+    P = problem(orc, f)
+    h = qpath.qp_build_qubo(f)
+    rng = np.random.default_rng(int(T0))
+    R = 12
+    init = (rng.random((R, P.n)) < 0.3).astype(np.uint8)
+    ref = orc.anneal_structured(P, R, 25, seed=17, init_states=init, T0=T0, T1=T1)
+    assert_same(gpu_anneal(h, R, 25, 17, T0=T0, T1=T1, init=init, kernel=kernel), ref)
+
+
 @pytest.mark.parametrize("kname,kernel", STRUCT_KERNELS)
 def test_structured_int32_distances(dev, orc, kname, kernel):  # 23 cells: every kernel fits
     """scale = 10000 forces int32 distances while the dE bound still fits."""
