@@ -96,8 +96,8 @@ template <typename DT, int NCH, int DMODE>
 __device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int (&base)[4], int &xnc, int validc,
                                        int (&tAc)[4], int &rt, int (&Cu)[NCH][4], uint32_t *row, long long &E,
                                        long long &acc, int &viol, const void *d, int Cp, int C, int lane, int twoA,
-                                       int len, unsigned lenm1, float cT, const uint32_t *thr, uint32_t rg,
-                                       uint32_t key0, uint32_t key1) {
+                                       int len, unsigned lenm1, float cT, int dq, uint32_t Q, const uint32_t *thr,
+                                       uint32_t rg, uint32_t key0, uint32_t key1) {
   const int ib = 128 * c + 4 * lane;
   const int delta = tC & 3;
   int cand = validc;
@@ -134,13 +134,21 @@ __device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int
         u1 = philox4x32_10(make_uint4(b0 + 1, (uint32_t)s, rg, kRngTag), key0, key1);
         h1 = true;
       }
+      uint32_t uw[4];
+      if (delta == 0) {  // the lane's four proposals are exactly one counter block
+        uw[0] = u0.x; uw[1] = u0.y; uw[2] = u0.z; uw[3] = u0.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int wsel = (delta + j) & 3;
+          uw[j] = (j < 4 - delta) ? word_of(u0, wsel) : word_of(u1, wsel);
+        }
+      }
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        if ((need >> j) & 1) {
-          const int wsel = (delta + j) & 3;
-          const uint32_t u = (j < 4 - delta) ? word_of(u0, wsel) : word_of(u1, wsel);
-          if (accept_draw(u, dE[j], cT, thr)) accm |= 1 << j;
-        }
+        // dE >= dq gives thr[dE] <= thr[dq] = Q, so u >= Q rejects outright
+        if (((need >> j) & 1) && (dE[j] < dq || uw[j] < Q) && accept_draw(uw[j], dE[j], cT, thr))
+          accm |= 1 << j;
       }
     }
     const uint32_t bal = __ballot_sync(kFull, accm);

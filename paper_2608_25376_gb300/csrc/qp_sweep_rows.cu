@@ -67,6 +67,11 @@ __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_
     const unsigned lenm1 = (unsigned)(len - 1);
     const unsigned hi = 0x80000000u - lenm1;
     const float cT = a.thr_c[ts];
+    // quick rejection: a draw u >= thr[dq] rejects every dE >= dq (thr is
+    // non-increasing); dq ~ 8 T ln 2 puts thr[dq] near 2^24, so almost every
+    // draw of a proposal with dE >= dq is rejected by two compares
+    const int dq = len > 1 ? min(len - 1, max(1, (int)fminf(8.0f / cT, 1.0e9f))) : 1;
+    const uint32_t Q = len > 1 ? __ldg(a.thr + a.thr_off[ts] + dq) : 0u;
     int P[NCH][4], Cu[NCH][4], N[NCH][4], Nn[NCH][4];
     zero<NCH>(P);
     zero<NCH>(Cu);
@@ -135,7 +140,8 @@ __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_
         }
         if (__any_sync(kFull, hit & validc[c]))
           flipped |= row_chunk<DT, NCH, DMODE>(c, t, s, tC, base, xn[c], validc[c], tAc[c], rt, Cu, row, E, acc,
-                                               viol, d, Cp, C, lane, twoA, len, lenm1, cT, thr, rg, a.key0, a.key1);
+                                               viol, d, Cp, C, lane, twoA, len, lenm1, cT, dq, Q, thr, rg,
+                                               a.key0, a.key1);
       }
       viol += (rt != 1) - (rt0 != 1);
       if (flipped) {
