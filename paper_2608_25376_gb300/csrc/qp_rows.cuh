@@ -41,6 +41,15 @@ __device__ __forceinline__ void add_drow(const void *d, int Cp, int C, int h, in
   }
 }
 
+template <typename DT, int NCH, int DMODE>
+__device__ __forceinline__ void set_drow(const void *d, int Cp, int C, int h, int lane, int (&F)[NCH][4]) {
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    const int i = 128 * c + 4 * lane;
+    drow4<DT, DMODE>(d, Cp, h, i, i < C, F[c]);
+  }
+}
+
 // F += sum over the set bits h of one row of d[h][.]; returns the number of bits
 // and, in *one, the cell when there is exactly one (else -1).
 template <typename DT, int NCH, int DMODE>
@@ -93,7 +102,8 @@ __device__ __forceinline__ int sel4(const int (&v)[4], int j) {
 // first accepted one, apply it, resume after it.  Returns whether any flip was
 // applied.
 template <typename DT, int NCH, int DMODE>
-__device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int (&base)[4], int &xnc, int validc,
+__device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int (&base)[4], const int (&de0)[4],
+                                       int &xnc, int validc,
                                        int (&tAc)[4], int &rt, int (&Cu)[NCH][4], uint32_t *row, long long &E,
                                        long long &acc, int &viol, const void *d, int Cp, int C, int lane, int twoA,
                                        int len, unsigned lenm1, float cT, int dq, uint32_t Q, const uint32_t *thr,
@@ -103,12 +113,11 @@ __device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int
   int cand = validc;
   bool h0 = false, h1 = false, flipped = false;
   uint4 u0 = make_uint4(0, 0, 0, 0), u1 = make_uint4(0, 0, 0, 0);
+  int dE[4] = {de0[0], de0[1], de0[2], de0[3]};  // for the row sum on entry
   while (true) {
-    const int k0 = twoA * (rt - 1), k1 = twoA * (3 - rt);
-    int accm = 0, need = 0, dE[4];
+    int accm = 0, need = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      dE[j] = ((xnc >> j) & 1) ? k1 - base[j] : base[j] + k0;
       const unsigned dm1 = (unsigned)(dE[j] - 1);
       accm |= (int)(dm1 >> 31) << j;   // dE <= 0
       need |= (int)(dm1 < lenm1) << j;  // 1 <= dE < len
@@ -176,6 +185,10 @@ __device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int
     add_drow<DT, NCH, DMODE>(d, Cp, C, 128 * c + 4 * L + jj, lane, dlt, Cu);
     cand &= lane < L ? 0 : (lane > L ? 0xF : (0xF << (jj + 1)) & 0xF);
     __syncwarp();
+    // the row sum moved: every later dE of the row moves with it
+    const int k0 = twoA * (rt - 1), k1 = twoA * (3 - rt);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) dE[j] = ((xnc >> j) & 1) ? k1 - base[j] : base[j] + k0;
   }
   return flipped;
 }

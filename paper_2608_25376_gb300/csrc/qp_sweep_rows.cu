@@ -65,7 +65,6 @@ __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_
     const uint32_t *thr = a.thr + a.thr_off[ts];
     const int len = a.thr_len[ts];
     const unsigned lenm1 = (unsigned)(len - 1);
-    const unsigned hi = 0x80000000u - lenm1;
     const float cT = a.thr_c[ts];
     // quick rejection: a draw u >= thr[dq] rejects every dE >= dq (thr is
     // non-increasing); dq ~ 8 T ln 2 puts thr[dq] near 2^24, so almost every
@@ -104,14 +103,13 @@ __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_
         xn[c] = xnn[c];
         rt += __popc(xn[c]);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          N[c][j] = Nn[c][j];
-          Nn[c][j] = 0;
-        }
+        for (int j = 0; j < 4; ++j) N[c][j] = Nn[c][j];
       }
-      if (t + 2 < C) {
-        if (h2 >= 0) add_drow<DT, NCH, DMODE>(d, Cp, C, h2, lane, 1, Nn);
-        else { int one; scan_row_field<DT, NCH, DMODE>(row + 2 * Cw, Cw, d, Cp, C, lane, Nn, &one); }
+      if (t + 2 < C && h2 >= 0) {
+        set_drow<DT, NCH, DMODE>(d, Cp, C, h2, lane, Nn);
+      } else {
+        zero<NCH>(Nn);
+        if (t + 2 < C) { int one; scan_row_field<DT, NCH, DMODE>(row + 2 * Cw, Cw, d, Cp, C, lane, Nn, &one); }
       }
       h2 = t + 3 < C ? hot1[t + 3] : -1;
 #pragma unroll
@@ -126,20 +124,20 @@ __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_
       for (int c = 0; c < NCH; ++c) {
         if (128 * c >= C) break;
         // base = B f + 2A c_i;  dE = base + 2A(r-1) (x = 0),  2A(3-r) - base (x = 1)
-        int base[4];
+        int base[4], de[4];
         unsigned hit = 0;
         {
           const int k0 = twoA * (rt - 1), k1 = twoA * (3 - rt);
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             base[j] = B * (P[c][j] + N[c][j]) + tAc[c][j];
-            const int de = ((xn[c] >> j) & 1) ? k1 - base[j] : base[j] + k0;
-            // dE <= 0 or 1 <= dE < len  <=>  (dE - 1 - (len - 1)) mod 2^32 >= 2^31 - (len - 1)
-            hit |= (unsigned)((unsigned)(de - 1) - lenm1 >= hi) << j;
+            de[j] = ((xn[c] >> j) & 1) ? k1 - base[j] : base[j] + k0;
+            // the proposal matters iff dE <= 0 (accepted) or 1 <= dE < len (a draw decides): dE < len
+            hit |= (unsigned)(de[j] < len) << j;
           }
         }
         if (__any_sync(kFull, hit & validc[c]))
-          flipped |= row_chunk<DT, NCH, DMODE>(c, t, s, tC, base, xn[c], validc[c], tAc[c], rt, Cu, row, E, acc,
+          flipped |= row_chunk<DT, NCH, DMODE>(c, t, s, tC, base, de, xn[c], validc[c], tAc[c], rt, Cu, row, E, acc,
                                                viol, d, Cp, C, lane, twoA, len, lenm1, cT, dq, Q, thr, rg,
                                                a.key0, a.key1);
       }
