@@ -159,7 +159,11 @@ qp_status qp_anneal(qp_handle *h, int32_t replicas, const qp_schedule *sched, ui
                     int64_t *best_out, void *cuda_stream);
 
 /* qp_anneal with options (opts may be NULL).  The kernel choice changes the
- * speed, never the result: both kernels follow the same sequential sweep. */
+ * speed, never the result: both kernels follow the same sequential sweep.
+ * The dense kernel brings each accepted flip's row of S into shared memory
+ * by a bulk copy when the buffers fit; a copy that has not completed after
+ * ~0.5 s ends its replica with energy INT64_MIN, and a synchronous call
+ * (some output in host memory) then returns QP_ETIMEOUT. */
 qp_status qp_anneal_ex(qp_handle *h, int32_t replicas, const qp_schedule *sched,
                        uint64_t seed, const uint8_t *init_states, uint8_t *states_out,
                        int64_t *energies_out, int64_t *best_out, const qp_anneal_opts *opts,

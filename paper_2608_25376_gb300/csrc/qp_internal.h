@@ -66,6 +66,7 @@ struct DenseArgs {
   uint8_t *states_out;
   int64_t *E_out, *best_out, *acc_out;
   int32_t *hbuf;             // R x np int32 when h lives in global memory
+  int32_t *err;              // set to 1 when a bulk row copy did not complete (nullable)
 };
 
 struct LaunchInfo {

@@ -291,28 +291,107 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32)
 // spins (bitset, shared) and, for path QUBOs, the row/column sums that decide
 // feasibility.  dE_k = (1 - 2x_k) h_k; an accepted flip of k streams row k of S
 // (= column k, S is symmetric) with 16-byte loads into h.
+// ---- bulk copies of S rows into shared memory (dense kernel)
+constexpr long long kBulkWaitCycles = 1000000000LL;  // ~0.5 s at 2 GHz, then give up
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// One thread asks for `bytes` (a multiple of 16, both addresses 16-byte
+// aligned) from global `src` into shared `dst`; the copy engine counts the
+// bytes on the mbarrier.  The proxy fence orders the warp's earlier reads of
+// dst before the asynchronous write.
+__device__ __forceinline__ void bulk_row_issue(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
+// Wait for phase `parity` of the mbarrier, giving up after kBulkWaitCycles.
+__device__ __forceinline__ bool bulk_wait(uint32_t mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > kBulkWaitCycles) return false;
+  }
+}
+
+// h += dlt * row, the row already staged in shared memory.
+template <typename ST>
+__device__ __forceinline__ void add_row_staged(int32_t *h, const ST *stage, int np, int dlt, int lane) {
+#pragma unroll 2
+  for (int c = lane * 8; c < np; c += 256) {
+    int v[8];
+    if (sizeof(ST) == 2) {
+      const int4 q = *reinterpret_cast<const int4 *>(stage + c);
+      v[0] = (int)(short)(q.x & 0xFFFF); v[1] = q.x >> 16;
+      v[2] = (int)(short)(q.y & 0xFFFF); v[3] = q.y >> 16;
+      v[4] = (int)(short)(q.z & 0xFFFF); v[5] = q.z >> 16;
+      v[6] = (int)(short)(q.w & 0xFFFF); v[7] = q.w >> 16;
+    } else {
+      const int4 q0 = *reinterpret_cast<const int4 *>(stage + c);
+      const int4 q1 = *(reinterpret_cast<const int4 *>(stage + c) + 1);
+      v[0] = q0.x; v[1] = q0.y; v[2] = q0.z; v[3] = q0.w;
+      v[4] = q1.x; v[5] = q1.y; v[6] = q1.z; v[7] = q1.w;
+    }
+    int4 *hp = reinterpret_cast<int4 *>(h + c);
+    int4 a0 = hp[0], a1 = hp[1];
+    a0.x += dlt * v[0]; a0.y += dlt * v[1]; a0.z += dlt * v[2]; a0.w += dlt * v[3];
+    a1.x += dlt * v[4]; a1.y += dlt * v[5]; a1.z += dlt * v[6]; a1.w += dlt * v[7];
+    hp[0] = a0;
+    hp[1] = a1;
+  }
+}
+
 template <typename ST>
 __device__ __forceinline__ void add_row(int32_t *h, const ST *row, int np, int dlt, int lane) {
+  if (sizeof(ST) == 2) {
+    // 8 loads of 16 bytes in flight per lane (4 KB per warp) before any use
+    constexpr int MLP = 8;
+    for (int c0 = lane * 8; c0 < np; c0 += 256 * MLP) {
+      int4 q[MLP];
+#pragma unroll
+      for (int b = 0; b < MLP; ++b) {
+        const int c = c0 + b * 256;
+        q[b] = c < np ? __ldg(reinterpret_cast<const int4 *>(row + c)) : make_int4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int b = 0; b < MLP; ++b) {
+        const int c = c0 + b * 256;
+        if (c < np) {
+          int4 *hp = reinterpret_cast<int4 *>(h + c);
+          int4 a0 = hp[0], a1 = hp[1];
+          a0.x += dlt * (int)(short)(q[b].x & 0xFFFF); a0.y += dlt * (q[b].x >> 16);
+          a0.z += dlt * (int)(short)(q[b].y & 0xFFFF); a0.w += dlt * (q[b].y >> 16);
+          a1.x += dlt * (int)(short)(q[b].z & 0xFFFF); a1.y += dlt * (q[b].z >> 16);
+          a1.z += dlt * (int)(short)(q[b].w & 0xFFFF); a1.w += dlt * (q[b].w >> 16);
+          hp[0] = a0;
+          hp[1] = a1;
+        }
+      }
+    }
+    return;
+  }
   for (int c0 = lane * 8; c0 < np; c0 += 1024) {
     int v[4][8];
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int c = c0 + b * 256;
       if (c < np) {
-        if (sizeof(ST) == 2) {
-          const int4 q = __ldg(reinterpret_cast<const int4 *>(row + c));
-          const int w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            v[b][2 * e] = (int)(short)(w[e] & 0xFFFF);
-            v[b][2 * e + 1] = w[e] >> 16;
-          }
-        } else {
-          const int4 q0 = __ldg(reinterpret_cast<const int4 *>(row + c));
-          const int4 q1 = __ldg(reinterpret_cast<const int4 *>(row + c) + 1);
-          v[b][0] = q0.x; v[b][1] = q0.y; v[b][2] = q0.z; v[b][3] = q0.w;
-          v[b][4] = q1.x; v[b][5] = q1.y; v[b][6] = q1.z; v[b][7] = q1.w;
-        }
+        const int4 q0 = __ldg(reinterpret_cast<const int4 *>(row + c));
+        const int4 q1 = __ldg(reinterpret_cast<const int4 *>(row + c) + 1);
+        v[b][0] = q0.x; v[b][1] = q0.y; v[b][2] = q0.z; v[b][3] = q0.w;
+        v[b][4] = q1.x; v[b][5] = q1.y; v[b][6] = q1.z; v[b][7] = q1.w;
       }
     }
 #pragma unroll
@@ -330,7 +409,10 @@ __device__ __forceinline__ void add_row(int32_t *h, const ST *row, int np, int d
   }
 }
 
-template <typename ST, bool H_SMEM>
+// BULK: an accepted flip's row of S comes into a per-warp shared buffer by one
+// bulk copy (cp.async.bulk, completion on an mbarrier) and is added from
+// there; otherwise the warp streams it with 16-byte loads.
+template <typename ST, bool H_SMEM, bool BULK>
 __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_sweep_dense(const DenseArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
@@ -342,10 +424,15 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_sweep_dense(const Dens
   uint32_t *fz = reinterpret_cast<uint32_t *>(smem);
   for (int w = threadIdx.x; w < nw_pad; w += blockDim.x) fz[w] = w < nw ? a.frozen_bits[w] : 0u;
   unsigned char *p = smem + 4 * (size_t)nw_pad;
-  const size_t per_warp = (H_SMEM ? 4 * (size_t)np : 0) + 4 * (size_t)nw_pad + (C > 0 ? 4 * (size_t)Cp : 0);
+  const size_t stage_bytes = BULK ? sizeof(ST) * (size_t)np + 16 : 0;  // row buffer + mbarrier
+  const size_t per_warp =
+      (H_SMEM ? 4 * (size_t)np : 0) + stage_bytes + 4 * (size_t)nw_pad + (C > 0 ? 4 * (size_t)Cp : 0);
   unsigned char *wp = p + warp * per_warp;
   int32_t *h = H_SMEM ? reinterpret_cast<int32_t *>(wp) : nullptr;
-  uint32_t *st = reinterpret_cast<uint32_t *>(wp + (H_SMEM ? 4 * (size_t)np : 0));
+  ST *stage = BULK ? reinterpret_cast<ST *>(wp + (H_SMEM ? 4 * (size_t)np : 0)) : nullptr;
+  const uint32_t mbar = BULK ? smem_addr(wp + (H_SMEM ? 4 * (size_t)np : 0) + sizeof(ST) * (size_t)np) : 0u;
+  uint32_t parity = 0;
+  uint32_t *st = reinterpret_cast<uint32_t *>(wp + (H_SMEM ? 4 * (size_t)np : 0) + stage_bytes);
   int16_t *rowsum = reinterpret_cast<int16_t *>(st + nw_pad);
   int16_t *colsum = rowsum + Cp;
   __syncthreads();
@@ -353,6 +440,13 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_sweep_dense(const Dens
   if (r >= a.R) return;  // no CTA-wide barrier after this point
   if (!H_SMEM) h = a.hbuf + (size_t)r * np;
   const uint32_t rg = (uint32_t)(a.rep_offset + r);
+  if (BULK) {
+    if (lane == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+  }
 
   // ---- initial state and local fields
   const uint8_t *init = a.init ? a.init + (size_t)r * n : nullptr;
@@ -471,7 +565,27 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_sweep_dense(const Dens
         const int dlt = 1 - 2 * (int)((xnL >> jj) & 1);
         E += de;
         ++acc;
-        add_row(h, S + (size_t)k * np, np, dlt, lane);
+        int32_t skk;
+        if (BULK) {
+          __syncwarp();
+          if (lane == 0) bulk_row_issue(smem_addr(stage), S + (size_t)k * np, (uint32_t)(sizeof(ST) * np), mbar);
+          const bool done = __all_sync(kFull, bulk_wait(mbar, parity));
+          parity ^= 1u;
+          if (!done) {
+            // the copy did not complete: flag it, let it land (bounded), drop this chain
+            if (lane == 0) {
+              if (a.err) atomicExch(a.err, 1);
+              bulk_wait(mbar, parity ^ 1u);
+              a.E_out[r] = LLONG_MIN;
+            }
+            return;
+          }
+          add_row_staged(h, stage, np, dlt, lane);
+          skk = (int32_t)stage[k];
+        } else {
+          add_row(h, S + (size_t)k * np, np, dlt, lane);
+          skk = 0;
+        }
         __syncwarp();
         int t = 0, i = 0, ro = 0, co = 0;
         if (C > 0) {
@@ -483,7 +597,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_sweep_dense(const Dens
         }
         __syncwarp();
         if (lane == 0) {
-          h[k] -= dlt * ld_elem(S + (size_t)k * np + k, false);
+          h[k] -= dlt * (BULK ? skk : ld_elem(S + (size_t)k * np + k, false));
           st[k >> 5] ^= 1u << (k & 31);
           if (C > 0) {
             rowsum[t] = (int16_t)(ro + dlt);
@@ -581,9 +695,9 @@ cudaError_t launch_s(const StructArgs &a, int W, size_t smem, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename ST, bool HS>
+template <typename ST, bool HS, bool BULK>
 cudaError_t launch_d(const DenseArgs &a, int W, size_t smem, cudaStream_t st) {
-  auto k = k_sweep_dense<ST, HS>;
+  auto k = k_sweep_dense<ST, HS, BULK>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int blocks = (a.R + W - 1) / W;
@@ -600,11 +714,12 @@ size_t structured_smem(int C, bool d_i16, int W, bool state_smem, bool d_smem) {
   return dbytes + W * per;
 }
 
-size_t dense_smem(int64_t n, int C, int W, bool h_smem) {
+size_t dense_smem(int64_t n, int C, int W, bool h_smem, size_t elem_bytes = 0) {
   const int np = round_up((int)n, 8);
   const int nw_pad = round_up((int)((n + 31) >> 5), 4);
   const int Cp = round_up(C > 0 ? C : 1, 8);
-  const size_t per = (h_smem ? 4 * (size_t)np : 0) + 4 * (size_t)nw_pad + (C > 0 ? 4 * (size_t)Cp : 0);
+  const size_t stage = elem_bytes ? elem_bytes * (size_t)np + 16 : 0;  // bulk row buffer + mbarrier
+  const size_t per = (h_smem ? 4 * (size_t)np : 0) + stage + 4 * (size_t)nw_pad + (C > 0 ? 4 * (size_t)Cp : 0);
   return 4 * (size_t)nw_pad + W * per;
 }
 
@@ -653,16 +768,22 @@ bool dense_h_fits_smem(int64_t n, int C, int W) { return dense_smem(n, C, W, tru
 cudaError_t launch_dense(const DenseArgs &a, bool s_i16, int W, cudaStream_t st, LaunchInfo *info) {
   const bool h_smem = dense_smem(a.n, a.C, W, true) <= kSmemLimit;
   if (!h_smem && a.hbuf == nullptr) return cudaErrorInvalidValue;
-  const size_t smem = dense_smem(a.n, a.C, W, h_smem);
+  const size_t eb = s_i16 ? 2 : 4;
+  const bool bulk = h_smem && dense_smem(a.n, a.C, W, true, eb) <= kSmemLimit;
+  const size_t smem = dense_smem(a.n, a.C, W, h_smem, bulk ? eb : 0);
   if (smem > kSmemLimit) return cudaErrorInvalidValue;
   if (info) {
     info->warps_per_cta = W;
     info->blocks = (a.R + W - 1) / W;
     info->smem = smem;
-    info->variant = h_smem ? "h:smem" : "h:global";
+    info->variant = bulk ? "h:smem, rows by bulk copy" : (h_smem ? "h:smem" : "h:global");
   }
-  if (s_i16) return h_smem ? launch_d<int16_t, true>(a, W, smem, st) : launch_d<int16_t, false>(a, W, smem, st);
-  return h_smem ? launch_d<int32_t, true>(a, W, smem, st) : launch_d<int32_t, false>(a, W, smem, st);
+  if (s_i16) {
+    if (bulk) return launch_d<int16_t, true, true>(a, W, smem, st);
+    return h_smem ? launch_d<int16_t, true, false>(a, W, smem, st) : launch_d<int16_t, false, false>(a, W, smem, st);
+  }
+  if (bulk) return launch_d<int32_t, true, true>(a, W, smem, st);
+  return h_smem ? launch_d<int32_t, true, false>(a, W, smem, st) : launch_d<int32_t, false, false>(a, W, smem, st);
 }
 
 cudaError_t launch_build_dense(void *S, bool s_i16, int32_t np, int32_t C, const int32_t *d32,

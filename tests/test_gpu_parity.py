@@ -377,6 +377,21 @@ def test_full_size_10x10_dense_sampled(dev, orc):
     assert_same(got, ref, idx)
 
 
+@pytest.mark.parametrize("rpc", [4, 5])
+def test_dense_row_staging_modes(dev, orc, rpc):
+    """The 10x10 field's dense sweep (n = 8464) with 4 replicas per CTA stages
+    accepted rows by bulk copy into shared memory; with 5 the row buffers no
+    longer fit and rows stream through registers.  Both match the oracle."""
+    f = inputs.WORKLOADS["10x10-p0.10"]["field"]()
+    P = problem(orc, f)
+    h = qpath.qp_build_qubo(f, flags=qpath.QP_DENSE | qpath.QP_STRUCTURED)
+    R = 11
+    got = gpu_anneal(h, R, 40, 5, T0=2000.0, T1=500.0, kernel=qpath.QP_KERNEL_DENSE, rpc=rpc)
+    ref = orc.anneal_structured(P, R, 40, T0=2000.0, T1=500.0, seed=5)
+    assert_same(got, ref)
+    assert ref.accepts.min() > 1000  # many rows staged per replica
+
+
 @pytest.mark.slow
 def test_full_size_24x24_structured_sampled(dev, orc):
     """24x24 field, 15% obstacles, 4096 replicas x 10000 sweeps, int16 d; two
