@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-replica-exchange", action="store_true")
     ap.add_argument("--replicas-per-cta", type=int, default=0)
     ap.add_argument("--structured-kernel", default="rows", choices=["rows", "flat"])
-    ap.add_argument("--profile-case", default=None, choices=["rows", "flat", "dense"],
+    ap.add_argument("--profile-case", default=None, choices=["rows", "flat", "dense", "mlp"],
                     help="run one warm-up and one measured launch of that kernel on a sub-range of "
                          "the workload (--sweep-window, --replicas), for ncu captures")
     ap.add_argument("--sweep-window", nargs=2, type=int, default=[0, 100])
@@ -546,6 +546,26 @@ def run_profile_case(args):
     from paper_2608_25376_gb300 import build as qbuild
     qbuild.build()
     from paper_2608_25376_gb300 import inputs, qpath
+    if args.profile_case == "mlp":
+        # one warm-up and one measured training step of the warm-start MLP on
+        # 16384 cells (64 fields of 256): 11 tensor-core GEMM launches a step
+        import numpy as np
+        M = 16384
+        rng = np.random.default_rng(0)
+        X = rng.random((M, qpath.WS_FEATURES), dtype=np.float32)
+        Y = rng.integers(0, qpath.WS_STEPS, M).astype(np.int32)
+        T = np.full(M, qpath.WS_STEPS, np.int32)
+        m = qpath.WarmStartModel(seed=1)
+        times = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            loss = qpath.qp_ws_train_step(m, X, Y, T, 1e-3)
+            torch.cuda.synchronize()
+            times.append((time.perf_counter() - t0) * 1e3)
+        print(json.dumps({"profile_case": "mlp", "cells": M, "ms": times, "loss": loss,
+                          "flops_per_layer_fwd": 2 * M * 256 * 256}))
+        return 0
     w = inputs.WORKLOADS[args.workload]
     f = w["field"]()
     kernel = {"rows": qpath.QP_KERNEL_STRUCTURED, "flat": qpath.QP_KERNEL_STRUCTURED_FLAT,
