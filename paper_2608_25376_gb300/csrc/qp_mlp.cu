@@ -5,17 +5,22 @@
 // Every matrix product (forward, dX = dY W, dW = dY^T X) runs on one tcgen05
 // kernel: D[M x N] (+)= A[M x K] B[N x K]^T with bf16 operands (both K-major,
 // i.e. K contiguous) and fp32 accumulation in tensor memory.  A CTA owns a
-// 128 x N tile (N <= 256, multiple of 16) and walks K in chunks of 64: its
-// threads copy the two operand chunks into shared memory in the canonical
-// no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix, core
-// matrices adjacent along K 128 B apart, 8-row groups 1024 B apart), one
-// elected thread issues the 128 x N x 16 MMAs and commits them to an mbarrier,
-// and everybody waits on it (bounded) before the chunk buffer is refilled.
-// The epilogue reads the accumulator back with tcgen05.ld (warp w owns TMEM
-// lanes 32w..32w+31 = rows of the tile) and applies bias/ReLU/masking.
-// Split-K partial tiles are added into an fp32 output with atomics.
+// 128 x N tile (N <= 256, multiple of 16) and walks K in chunks of 64 through
+// two shared-memory stages: one thread has the tensor-memory-access engine
+// load each operand chunk (one 2-D tile copy per operand, 128-byte swizzle,
+// zeros outside the matrix) with its byte count on the stage's "full"
+// mbarrier, issues the 128 x N x 16 MMAs of the chunk once it has landed and
+// commits them to the stage's "done" mbarrier, which frees the stage for the
+// chunk after next; the load of chunk c+1 overlaps the MMAs of chunk c.
+// Every wait is bounded.  The epilogue reads the accumulator back with
+// tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = rows of the tile) and
+// applies bias/ReLU/masking.  Split-K partial tiles are added into an fp32
+// output with atomics.
+#include <cuda.h>  // CUtensorMap and the tile-encoder types; the encoder comes from the runtime
 #include <cuda_bf16.h>
 #include <stdint.h>
+
+#include <mutex>
 
 #include "qp_mlp.h"
 
@@ -26,27 +31,49 @@ namespace {
 constexpr int kTileM = 128;
 constexpr int kChunkK = 64;
 constexpr int kTmemCols = 256;
-constexpr size_t kSmemA = kTileM * kChunkK * 2;  // 16 KB
-constexpr size_t kSmemB = 256 * kChunkK * 2;     // 32 KB
-// 100 KB of dynamic shared memory keeps at most two CTAs (2 x 256 TMEM
-// columns = all 512) on an SM, so tcgen05.alloc never has to wait long.
+constexpr size_t kSmemA = kTileM * kChunkK * 2;  // 16 KB per stage
+constexpr size_t kSmemB = 256 * kChunkK * 2;     // 32 KB per stage
+constexpr int kStages = 2;
+// Two stages (96 KB) plus 1 KB to align them to the 1024-byte swizzle
+// pattern; 100 KB keeps at most two CTAs (2 x 256 TMEM columns = all 512) on
+// an SM, so tcgen05.alloc never has to wait long.
 constexpr size_t kGemmSmem = 100 * 1024;
+static_assert(kStages * (kSmemA + kSmemB) + 1024 <= kGemmSmem, "GEMM stages exceed the shared-memory budget");
 constexpr long long kWaitCycles = 1000000000LL;  // ~0.5 s at 2 GHz, then give up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Shared-memory matrix descriptor (tcgen05): start address >> 4 in bits 0-13,
-// leading-dimension byte offset >> 4 in 16-29, stride-dimension byte offset
-// >> 4 in 32-45, descriptor version 1 in 46-47, no swizzle (bits 61-63 = 0).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor (tcgen05) of a K-major operand tile that
+// the tile copy wrote with 128-byte swizzle: row r is 128 bytes (64 bf16 along
+// K) at r * 128 with its 16-byte pieces permuted within each 8-row, 1024-byte
+// group.  Start address >> 4 in bits 0-13, leading-dimension offset field 1
+// (not used by swizzled K-major tiles), stride-dimension offset 1024 >> 4 (one
+// 8-row group) in 32-45, descriptor version 1 in 46-47, base offset 0 (tiles
+// are 1024-byte aligned), layout type 2 = 128-byte swizzle in bits 61-63.  The
+// k-th 16-element step of a chunk starts 32k bytes into the tile.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
   d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
   return d;
+}
+
+// 2-D tile copy global -> shared of box (x, y) = (k0, row0) of `map`, its bytes
+// counted on `mbar`.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
 }
 
 // Instruction descriptor of kind::f16: fp32 D (bits 4-5 = 1), bf16 A and B
@@ -113,6 +140,22 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
+// 32 consecutive fp32 columns of this thread's TMEM lane (one load, one wait).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // 16 consecutive fp32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
@@ -126,101 +169,146 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// rows [row0, row0 + nrows) x columns [k0, k0 + 64) of a row-major bf16 matrix
-// into the core-matrix layout; columns at or beyond kend (and rows beyond
-// nvalid) read as zero.  K offsets are multiples of 8 elements (16 B).
-__device__ __forceinline__ void stage_chunk(uint8_t *dst, const __nv_bfloat16 *src, int ld, int row0, int nrows,
-                                            int nvalid, int k0, int kend, int tid, int nthreads) {
-  for (int idx = tid; idx < nrows * 8; idx += nthreads) {
-    const int r = idx >> 3, seg = idx & 7;
-    const int m = row0 + r, k = k0 + seg * 8;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (m < nvalid && k < kend) v = __ldg(reinterpret_cast<const uint4 *>(src + (size_t)m * ld + k));
-    *reinterpret_cast<uint4 *>(dst + ((r >> 3) * 8 + seg) * 128 + (r & 7) * 16) = v;
-  }
-}
-
-__global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g) {
-  extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ uint64_t mbar;
+__global__ void __launch_bounds__(128)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t full[kStages], done[kStages];
   __shared__ uint32_t tmem_slot;
   __shared__ int fail_flag;
-  uint8_t *sA = smem;
-  uint8_t *sB = smem + kSmemA;
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * kTileM;
   const int N = g.N;
   const int kbeg = blockIdx.z * g.k_per_split;
   const int kend = min(g.K, kbeg + g.k_per_split);
+  const int nchunks = kend > kbeg ? (kend - kbeg + kChunkK - 1) / kChunkK : 0;
 
   if (warp == 0) tmem_alloc(smem_u32(&tmem_slot), kTmemCols);
   if (tid == 0) {
-    mbar_init(smem_u32(&mbar), 1);
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&done[s]), 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
     fail_flag = 0;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  const uint32_t idesc = idesc_bf16(kTileM, N);
-  uint32_t parity = 0;
-  int issued = 0;
-  for (int k0 = kbeg; k0 < kend; k0 += kChunkK) {
-    stage_chunk(sA, g.A, g.lda, m0, kTileM, g.M, k0, kend, tid, 128);
-    stage_chunk(sB, g.B, g.ldb, 0, N, N, k0, kend, tid, 128);
-    proxy_fence();
-    __syncthreads();
-    if (tid == 0) {
+  const int issued = nchunks;
+  if (tid == 0 && nchunks > 0) {
+    const uint32_t idesc = idesc_bf16(kTileM, N);
+    const uint32_t bytes = (uint32_t)(kSmemA + (size_t)N * kChunkK * 2);  // both boxes, zeros included
+    uint32_t sa[kStages], sb[kStages];
+    for (int s = 0; s < kStages; ++s) {
+      sa[s] = smem_u32(smem + s * kSmemA);
+      sb[s] = smem_u32(smem + kStages * kSmemA + s * kSmemB);
+    }
+    // completions issued and seen per barrier; the k-th completion has parity k & 1
+    int full_issued[kStages] = {0, 0}, full_seen[kStages] = {0, 0};
+    int done_issued[kStages] = {0, 0}, done_seen[kStages] = {0, 0};
+    bool ok = true;
+    auto load = [&](int c) {
+      const int s = c & 1;
+      mbar_expect_tx(smem_u32(&full[s]), bytes);
+      tma_load_2d(sa[s], &tmA, kbeg + c * kChunkK, m0, smem_u32(&full[s]));
+      tma_load_2d(sb[s], &tmB, kbeg + c * kChunkK, 0, smem_u32(&full[s]));
+      ++full_issued[s];
+    };
+    load(0);
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int s = c & 1;
+      if (c + 1 < nchunks) {
+        const int s1 = (c + 1) & 1;
+        if (done_seen[s1] < done_issued[s1]) {  // the MMAs of chunk c-1 still read stage s1
+          ok = mbar_wait(smem_u32(&done[s1]), done_seen[s1] & 1);
+          if (!ok) break;
+          ++done_seen[s1];
+        }
+        load(c + 1);
+      }
+      ok = mbar_wait(smem_u32(&full[s]), full_seen[s] & 1);
+      if (!ok) break;
+      ++full_seen[s];
       tc_fence_after();
+      const int k0 = kbeg + c * kChunkK;
       const int ksteps = min(4, (kend - k0 + 15) / 16);
       for (int kk = 0; kk < ksteps; ++kk) {
-        const uint64_t ad = smem_desc(smem_u32(sA) + kk * 256, 128, 1024);
-        const uint64_t bd = smem_desc(smem_u32(sB) + kk * 256, 128, 1024);
-        mma_bf16(tmem, ad, bd, idesc, (issued > 0 || kk > 0) ? 1u : 0u);
+        const uint64_t ad = smem_desc_sw128(sa[s] + kk * 32);
+        const uint64_t bd = smem_desc_sw128(sb[s] + kk * 32);
+        mma_bf16(tmem, ad, bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
       }
-      mma_commit(smem_u32(&mbar));
+      mma_commit(smem_u32(&done[s]));
+      ++done_issued[s];
     }
-    ++issued;
-    const bool ok = mbar_wait(smem_u32(&mbar), parity);
-    parity ^= 1u;
+    // the accumulator is complete once every commit has landed; after a
+    // failed wait, let whatever is still in flight land (bounded) before the
+    // CTA frees its shared and tensor memory
+    for (int s = 0; s < kStages; ++s) {
+      while (done_seen[s] < done_issued[s]) {
+        if (!mbar_wait(smem_u32(&done[s]), done_seen[s] & 1)) { ok = false; break; }
+        ++done_seen[s];
+      }
+      while (full_seen[s] < full_issued[s]) {
+        if (!mbar_wait(smem_u32(&full[s]), full_seen[s] & 1)) { ok = false; break; }
+        ++full_seen[s];
+      }
+    }
     if (!ok) fail_flag = 1;
-    __syncthreads();
-    if (fail_flag) break;
   }
+  __syncthreads();
   tc_fence_after();
   if (!fail_flag && issued > 0) {
     const int row = m0 + warp * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < N; c0 += 16) {
-      float v[16];
-      tmem_ld16(lane_base + c0, v);
-      if (row >= g.M) continue;
-      if (g.mode == kEpiBiasRelu || g.mode == kEpiBiasF32) {
+    for (int c0 = 0; c0 < N; c0 += 32) {  // N is a multiple of 16: the last block may be half used
+      float v[32];
+      const int nc = min(32, N - c0);
+      if (nc == 32) {
+        tmem_ld32(lane_base + c0, v);
+      } else {
+        float w[16];
+        tmem_ld16(lane_base + c0, w);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] += g.bias ? g.bias[c0 + i] : 0.0f;
+        for (int i = 0; i < 16; ++i) v[i] = w[i];
       }
-      if (g.mode == kEpiBiasRelu) {
-        __nv_bfloat16 *o = g.out_bf16 + (size_t)row * g.ldo + c0;
+      if (row >= g.M) continue;
 #pragma unroll
-        for (int i = 0; i < 16; i += 2)
-          *reinterpret_cast<__nv_bfloat162 *>(o + i) = __floats2bfloat162_rn(fmaxf(v[i], 0.0f), fmaxf(v[i + 1], 0.0f));
-      } else if (g.mode == kEpiBiasF32) {
-        float *o = g.out_f32 + (size_t)row * g.ldo + c0;
+      for (int q = 0; q < 2; ++q) {
+        if (q * 16 >= nc) break;
+        const int cc = c0 + q * 16;
+        float *vv = v + q * 16;
+        if (g.mode == kEpiBiasRelu || g.mode == kEpiBiasF32) {
 #pragma unroll
-        for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4 *>(o + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-      } else if (g.mode == kEpiAtomicF32) {
-        float *o = g.out_f32 + (size_t)row * g.ldo + c0;
+          for (int i = 0; i < 16; ++i) vv[i] += g.bias ? g.bias[cc + i] : 0.0f;
+        }
+        if (g.mode == kEpiBiasRelu) {
+          __nv_bfloat16 *o = g.out_bf16 + (size_t)row * g.ldo + cc;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) atomicAdd(o + i, v[i]);
-      } else {  // kEpiReluMask: gradient through the ReLU of a stored activation
-        const __nv_bfloat16 *ref = g.relu_ref + (size_t)row * g.ldr + c0;
-        __nv_bfloat16 *o = g.out_bf16 + (size_t)row * g.ldo + c0;
+          for (int i = 0; i < 16; i += 2)
+            *reinterpret_cast<__nv_bfloat162 *>(o + i) =
+                __floats2bfloat162_rn(fmaxf(vv[i], 0.0f), fmaxf(vv[i + 1], 0.0f));
+        } else if (g.mode == kEpiBiasF32) {
+          float *o = g.out_f32 + (size_t)row * g.ldo + cc;
 #pragma unroll
-        for (int i = 0; i < 16; i += 2) {
-          const float a = __bfloat162float(ref[i]) > 0.0f ? v[i] : 0.0f;
-          const float b = __bfloat162float(ref[i + 1]) > 0.0f ? v[i + 1] : 0.0f;
-          *reinterpret_cast<__nv_bfloat162 *>(o + i) = __floats2bfloat162_rn(a, b);
+          for (int i = 0; i < 16; i += 4)
+            *reinterpret_cast<float4 *>(o + i) = make_float4(vv[i], vv[i + 1], vv[i + 2], vv[i + 3]);
+        } else if (g.mode == kEpiAtomicF32) {
+          float *o = g.out_f32 + (size_t)row * g.ldo + cc;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) atomicAdd(o + i, vv[i]);
+        } else {  // kEpiReluMask: gradient through the ReLU of a stored activation
+          const __nv_bfloat16 *ref = g.relu_ref + (size_t)row * g.ldr + cc;
+          __nv_bfloat16 *o = g.out_bf16 + (size_t)row * g.ldo + cc;
+#pragma unroll
+          for (int i = 0; i < 16; i += 2) {
+            const float a = __bfloat162float(ref[i]) > 0.0f ? vv[i] : 0.0f;
+            const float b = __bfloat162float(ref[i + 1]) > 0.0f ? vv[i + 1] : 0.0f;
+            *reinterpret_cast<__nv_bfloat162 *>(o + i) = __floats2bfloat162_rn(a, b);
+          }
         }
       }
     }
@@ -330,22 +418,61 @@ __global__ void k_f32_to_bf16(const float *in, __nv_bfloat16 *out, int n) {
 
 }  // namespace
 
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tile-map encoder, looked up once through the runtime.
+EncodeTiled encoder() {
+  static std::once_flag once;
+  static EncodeTiled fn = nullptr;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  });
+  return fn;
+}
+
+// Row-major bf16 matrix [rows x K] with row stride ld (elements) as tiles of
+// 64 (K) x box_rows, 128-byte swizzle, zeros outside the matrix.
+bool tile_map(CUtensorMap *map, const __nv_bfloat16 *base, int rows, int K, int ld, int box_rows) {
+  EncodeTiled enc = encoder();
+  if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) || ((size_t)ld * 2) % 16) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kChunkK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
 cudaError_t gemm(const GemmArgs &g, int splits, cudaStream_t st) {
   if (g.N < 16 || g.N > 256 || (g.N & 15) || (g.K & 15) || (g.lda & 7) || (g.ldb & 7) || splits < 1)
     return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  alignas(64) CUtensorMap ta, tb;
+  if (!tile_map(&ta, g.A, g.M, g.K, g.lda, kTileM) || !tile_map(&tb, g.B, g.N, g.K, g.ldb, g.N))
+    return cudaErrorInvalidValue;
   GemmArgs a = g;
   int kps = (g.K + splits - 1) / splits;
   kps = (kps + kChunkK - 1) / kChunkK * kChunkK;
   a.k_per_split = kps;
   const int zs = (g.K + kps - 1) / kps;
   dim3 grid((g.M + kTileM - 1) / kTileM, 1, zs);
-  k_gemm_tc<<<grid, 128, kGemmSmem, st>>>(a);
+  k_gemm_tc<<<grid, 128, kGemmSmem, st>>>(ta, tb, a);
   return cudaGetLastError();
 }
 
