@@ -99,11 +99,21 @@ enum {
   QP_KERNEL_STRUCTURED_GROUP = 5
 };
 
+/* qp_anneal_opts.flags.  QP_ANNEAL_SKIP_SETTLED lets the row-parallel kernel
+ * (fields of up to 512 cells, also in qp_batch_*) skip a sweep whose outcome
+ * is already known: once a sweep of a replica met no proposal with dE < len
+ * (none accepted outright, none needing a draw), its state cannot change in
+ * any later sweep whose table is no longer (len non-increasing, as on a
+ * cooling schedule), so those sweeps are not evaluated.  Results are
+ * identical bit for bit; only the time changes.  Other kernels ignore it. */
+enum { QP_ANNEAL_SKIP_SETTLED = 1 };
+
 typedef struct {
   int32_t kernel;            /* QP_KERNEL_*; AUTO = structured when built     */
   int32_t replicas_per_cta;  /* warps (= replicas) per CTA; 0 = tuned default */
   int32_t replica_offset;    /* global index of replica 0 (its RNG stream)    */
   int64_t *accepts_out;      /* optional [R]: accepted flips per replica      */
+  int32_t flags;             /* QP_ANNEAL_* bits                              */
 } qp_anneal_opts;
 
 /* Section II and Eqs. 3-6 (Algorithm 1, first five steps): build the path
@@ -206,11 +216,13 @@ qp_status qp_anneal_noalloc(qp_handle *h, int32_t replicas, const qp_schedule *s
  * qp_batch_destroy frees it.  The handles and output buffers must outlive the
  * batch.  Taking work is one atomic add per (field, replica): no device wait.
  * opts (NULL = defaults): replicas_per_cta (warps per CTA) and ctas (grid
- * size, 0 = as many as fit on the GPU at once); the autotuner picks them. */
+ * size, 0 = as many as fit on the GPU at once), which the autotuner picks,
+ * and flags (QP_ANNEAL_SKIP_SETTLED, same results). */
 typedef struct qp_batch qp_batch;
 typedef struct {
   int32_t replicas_per_cta;
   int32_t ctas;
+  int32_t flags;  /* QP_ANNEAL_SKIP_SETTLED or 0 */
 } qp_batch_opts;
 qp_status qp_batch_create(qp_handle *const *hs, int32_t count, int32_t replicas, const qp_schedule *sched,
                           uint64_t seed, uint8_t *const *states_out, int64_t *const *energies_out,
@@ -281,6 +293,7 @@ qp_status qp_repair_path(const qp_handle *h, const uint8_t *state, int32_t max_p
  *   their threshold tables are reused.  Round k anneals fresh chains with
  *   replica indices k*R .. k*R+R-1; a round starts while the previous round's
  *   duration still fits in the budget (round 0 always runs).
+ * The sweeps run with QP_ANNEAL_SKIP_SETTLED (same results, less time).
  * Given info->n_sweeps and info->rounds the result is reproducible: it equals
  * qp_anneal_ex over sweeps [0, n_sweeps) with replica_offset k*R for each
  * round k, qp_repair_batch of each round's states, and the shortest path

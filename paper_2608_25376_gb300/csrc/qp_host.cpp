@@ -548,6 +548,7 @@ extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc
     a.key0 = key0; a.key1 = key1;
     a.thr = sched.thr; a.thr_off = sched.off; a.thr_len = sched.len; a.thr_c = sched.c;
     a.init = init_d; a.states_out = st_d; a.E_out = e_d; a.best_out = b_d; a.acc_out = a_d;
+    a.skip_settled = (o.flags & QP_ANNEAL_SKIP_SETTLED) ? 1 : 0;
     if (kernel == QP_KERNEL_STRUCTURED_GROUP) {
       if (group_size_for(h->C) < 2) return fail(QP_EINVAL, "the grouped kernel takes fields of up to 128 cells");
       int Wg = W;
@@ -942,6 +943,7 @@ extern "C" qp_status qp_anneal_timed(qp_handle *h, int32_t R, const qp_schedule 
     part.sweep_end = e;
     qp_anneal_opts o{};
     o.replica_offset = offset;
+    o.flags = QP_ANNEAL_SKIP_SETTLED;  // same results, settled sweeps cost nothing
     return qp_anneal_ex(h, R, &part, seed, init, out, E, nullptr, &o, st);
   };
 
@@ -1105,6 +1107,7 @@ extern "C" qp_status qp_batch_create(qp_handle *const *hs, int32_t count, int32_
     a.states_out = states_out[f]; a.E_out = energies_out[f];
     a.best_out = best_out ? best_out[f] : nullptr;
     a.acc_out = nullptr;
+    a.skip_settled = (o.flags & QP_ANNEAL_SKIP_SETTLED) ? 1 : 0;
   }
   // work units, largest fields first
   std::vector<int> order(count);

@@ -45,6 +45,8 @@ struct StructArgs {
   // Replica exchange: the table row replica r (local index) uses in every
   // sweep of the launch (its ladder level); null = row s for sweep s.
   const int32_t *level;
+  // QP_ANNEAL_SKIP_SETTLED: skip sweeps that provably change nothing
+  int32_t skip_settled;
 };
 
 // Arguments of the dense sweep (one warp = one replica).

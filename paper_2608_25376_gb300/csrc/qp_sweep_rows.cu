@@ -60,10 +60,18 @@ __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_
 
   // ---- sweeps
   const int lev = a.level ? __ldg(a.level + r) : -1;
+  // A sweep that met no proposal with dE < len leaves the state as it was, so
+  // every later sweep with a table no longer than len does too (each of its
+  // proposals sees the same state and the same dE): those sweeps are skipped
+  // when asked to (results unchanged).
+  bool settled = false;
+  int settled_len = 0;
   for (int s = a.sweep_begin; s < a.sweep_end; ++s) {
     const int ts = lev >= 0 ? lev : s;  // table row: the sweep, or the replica's ladder level
     const uint32_t *thr = a.thr + a.thr_off[ts];
     const int len = a.thr_len[ts];
+    if (settled && len <= settled_len) continue;
+    bool any_hit = false;
     const unsigned lenm1 = (unsigned)(len - 1);
     const float cT = a.thr_c[ts];
     // quick rejection: a draw u >= thr[dq] rejects every dE >= dq (thr is
@@ -136,10 +144,12 @@ __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_
             hit |= (unsigned)(de[j] < len) << j;
           }
         }
-        if (__any_sync(kFull, hit & validc[c]))
+        if (__any_sync(kFull, hit & validc[c])) {
+          any_hit = true;
           flipped |= row_chunk<DT, NCH, DMODE>(c, t, s, tC, base, de, xn[c], validc[c], tAc[c], rt, Cu, row, E, acc,
                                                viol, d, Cp, C, lane, twoA, len, lenm1, cT, dq, Q, thr, rg,
                                                a.key0, a.key1);
+        }
       }
       viol += (rt != 1) - (rt0 != 1);
       if (flipped) {
@@ -156,6 +166,8 @@ __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_
         }
     }
     if (viol == 0 && E < best) best = E;
+    settled = a.skip_settled && !any_hit;
+    settled_len = len;
   }
 
   // ---- outputs

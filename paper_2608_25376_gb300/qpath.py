@@ -22,6 +22,7 @@ QP_OK, QP_EINVAL, QP_ENOMEM, QP_ERANGE, QP_ECUDA, QP_ETIMEOUT, QP_EINFEASIBLE = 
 QP_DENSE, QP_STRUCTURED, QP_DIST_I16 = 1, 2, 4
 QP_KERNEL_AUTO, QP_KERNEL_DENSE, QP_KERNEL_STRUCTURED, QP_KERNEL_STRUCTURED_FLAT = 0, 1, 2, 3
 QP_KERNEL_STRUCTURED_ROWS, QP_KERNEL_STRUCTURED_GROUP = 4, 5
+QP_ANNEAL_SKIP_SETTLED = 1
 E_NONE = np.iinfo(np.int64).max
 
 # every entry point include/qpath.h declares
@@ -49,7 +50,7 @@ class qp_schedule(ct.Structure):
 
 
 class qp_batch_opts(ct.Structure):
-    _fields_ = [("replicas_per_cta", ct.c_int32), ("ctas", ct.c_int32)]
+    _fields_ = [("replicas_per_cta", ct.c_int32), ("ctas", ct.c_int32), ("flags", ct.c_int32)]
 
 
 class qp_timed_info(ct.Structure):
@@ -69,7 +70,7 @@ def pt_schedule(levels, T_lo, T_hi, sweeps_per_exchange, exchanges) -> qp_pt_sch
 
 class qp_anneal_opts(ct.Structure):
     _fields_ = [("kernel", ct.c_int32), ("replicas_per_cta", ct.c_int32), ("replica_offset", ct.c_int32),
-                ("accepts_out", ct.c_void_p)]
+                ("accepts_out", ct.c_void_p), ("flags", ct.c_int32)]
 
 
 def lib_path() -> str:
@@ -249,9 +250,10 @@ def qp_anneal(h: Handle, replicas, sched, seed, init_states, states_out, energie
 
 
 def qp_anneal_ex(h: Handle, replicas, sched, seed, init_states, states_out, energies_out, best_out=None,
-                 kernel=QP_KERNEL_AUTO, replicas_per_cta=0, replica_offset=0, accepts_out=None, stream=None):
+                 kernel=QP_KERNEL_AUTO, replicas_per_cta=0, replica_offset=0, accepts_out=None, stream=None,
+                 flags=0):
     o = qp_anneal_opts(int(kernel), int(replicas_per_cta), int(replica_offset),
-                       None if accepts_out is None else _ptr(accepts_out).value)
+                       None if accepts_out is None else _ptr(accepts_out).value, int(flags))
     _check(lib().qp_anneal_ex(h.ptr, int(replicas), ct.byref(sched), ct.c_uint64(seed), _ptr(init_states),
                               _ptr(states_out), _ptr(energies_out), _ptr(best_out), ct.byref(o),
                               _stream(stream)))
@@ -300,11 +302,11 @@ class Batch:
 
 
 def qp_batch_create(handles, replicas, sched, seed, states_out, energies_out, best_out=None,
-                    replicas_per_cta=0, ctas=0) -> Batch:
+                    replicas_per_cta=0, ctas=0, flags=0) -> Batch:
     hs = (ct.c_void_p * len(handles))(*[h.ptr.value for h in handles])
     so, eo = _ptr_array(states_out), _ptr_array(energies_out)
     bo = None if best_out is None else _ptr_array(best_out)
-    o = qp_batch_opts(int(replicas_per_cta), int(ctas))
+    o = qp_batch_opts(int(replicas_per_cta), int(ctas), int(flags))
     out = ct.c_void_p()
     _check(lib().qp_batch_create(hs, len(handles), int(replicas), ct.byref(sched), ct.c_uint64(seed), so, eo,
                                  bo, ct.byref(o), ct.byref(out)))

@@ -91,6 +91,21 @@ def test_batch_configurations(dev, rpc, ctas):
     check_fields(handles, R, sc, seed, st, E, B)
 
 
+def test_batch_skip_settled_same_results(dev):
+    """A whole cooling schedule, settled sweeps skipped: same as the full run."""
+    import torch
+    fields = inputs.batch(10, seed=31)
+    handles = [qpath.qp_build_qubo(f) for f in fields]
+    R, seed = 12, 8
+    sc = qpath.schedule(1500)
+    st, E, B = outputs(handles, R)
+    b = qpath.qp_batch_create(handles, R, sc, seed, st, E, B, flags=qpath.QP_ANNEAL_SKIP_SETTLED)
+    b.run(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    check_fields(handles, R, sc, seed, st, E, B)
+    b.close()
+
+
 def test_batch_mixed_sizes_up_to_512_cells(dev):
     import torch
     fields = [inputs.rect(3, 3), inputs.obstacles(18, 18, 0.1, seed=8, start=5), inputs.rect(1, 2),

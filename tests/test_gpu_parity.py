@@ -377,6 +377,33 @@ def test_full_size_10x10_dense_sampled(dev, orc):
     assert_same(got, ref, idx)
 
 
+@pytest.mark.parametrize("name,f,R,S", [("6x6-p0.2", inputs.obstacles(6, 6, 0.2, seed=3, start=14), 40, 3000),
+                                         ("3x5-start7", inputs.rect(3, 5, start=7), 33, 1500),
+                                         ("13x13-p0.1", inputs.obstacles(13, 13, 0.1, seed=5, start=20), 6, 1200)])
+def test_skip_settled_same_results(dev, orc, name, f, R, S):
+    """Whole schedules (cooling to T = 1, so replicas settle): skipping settled
+    sweeps changes nothing, against the oracle and against the full kernel."""
+    P = problem(orc, f)
+    h = qpath.qp_build_qubo(f)
+    import torch
+    n = P.n
+    outs = []
+    for flags in (0, qpath.QP_ANNEAL_SKIP_SETTLED):
+        st = torch.zeros((R, n), dtype=torch.uint8, device="cuda")
+        E = torch.zeros(R, dtype=torch.int64, device="cuda")
+        B = torch.zeros(R, dtype=torch.int64, device="cuda")
+        A = torch.zeros(R, dtype=torch.int64, device="cuda")
+        qpath.qp_anneal_ex(h, R, qpath.schedule(S), 9, None, st, E, B, kernel=qpath.QP_KERNEL_STRUCTURED_ROWS,
+                           accepts_out=A, flags=flags, stream=torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        outs.append((st.cpu().numpy(), E.cpu().numpy(), B.cpu().numpy(), A.cpu().numpy()))
+    for a, b in zip(outs[0], outs[1]):
+        assert (a == b).all()
+    idx = [0, R - 1]
+    ref = orc.anneal_structured(P, idx, S, seed=9)
+    assert_same(outs[1], ref, idx)
+
+
 @pytest.mark.parametrize("rpc", [4, 5])
 def test_dense_row_staging_modes(dev, orc, rpc):
     """The 10x10 field's dense sweep (n = 8464) with 4 replicas per CTA stages
