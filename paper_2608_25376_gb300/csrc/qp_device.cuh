@@ -57,5 +57,48 @@ __device__ __forceinline__ bool accept_draw(uint32_t u, int dE, float c, const u
   return u < __ldg(thr + dE);
 }
 
+// ---- bulk copies global -> shared with mbarrier completion
+constexpr long long kBulkWaitCycles = 1000000000LL;  // ~0.5 s at 2 GHz, then give up
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init1(uint32_t mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One thread asks for `bytes` (a multiple of 16, both addresses 16-byte
+// aligned) from global `src` into shared `dst`; the copy engine counts the
+// bytes on the mbarrier.  The proxy fence orders the thread's (and, after a
+// __syncwarp, its warp's) earlier reads of dst before the asynchronous write.
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
+// Wait for phase `parity` of the mbarrier, giving up after kBulkWaitCycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > kBulkWaitCycles) return false;
+  }
+}
+
 }  // namespace dev
 }  // namespace qp

@@ -240,7 +240,7 @@ struct qp_handle {
   std::vector<uint8_t> frozen_host, fval_host;  // generic QUBOs
   // scratch
   DevBuf gstate, hbuf, in_stage, st_stage, e_stage, b_stage, a_stage, p_stage, l_stage, r_stage;
-  DevBuf dense_err;  // int32 flag: a bulk row copy of the dense sweep did not complete
+  DevBuf kernel_err;  // int32 flag: a bulk row copy of the dense sweep did not complete
   DevBuf t_states[2], t_E, t_paths, t_len, t_stat;  // qp_anneal_timed
   DevBuf pt_states[2], pt_E, pt_bseg, pt_best, pt_level, pt_owner, pt_swaps;  // qp_anneal_pt
 };
@@ -537,7 +537,7 @@ extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc
   const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
 
   LaunchInfo info;
-  bool dense_launched = false;
+  bool err_armed = false;
   if (structured) {
     int W = o.replicas_per_cta ? o.replicas_per_cta : 4;
     StructArgs a{};
@@ -573,11 +573,11 @@ extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc
       QP_TRY(h->hbuf.ensure((size_t)R * h->np * 4));
       a.hbuf = h->hbuf.as<int32_t>();
     }
-    QP_TRY(h->dense_err.ensure(4));
-    QP_CU(cudaMemsetAsync(h->dense_err.p, 0, 4, st));
-    a.err = h->dense_err.as<int32_t>();
+    QP_TRY(h->kernel_err.ensure(4));
+    QP_CU(cudaMemsetAsync(h->kernel_err.p, 0, 4, st));
+    a.err = h->kernel_err.as<int32_t>();
     QP_CU(launch_dense(a, h->S_i16, W, st, &info));
-    dense_launched = true;
+    err_armed = true;
   }
 launched:
   if (st_host) QP_CU(cudaMemcpyAsync(states_out, st_d, (size_t)R * n, cudaMemcpyDeviceToHost, st));
@@ -586,9 +586,9 @@ launched:
   if (a_host) QP_CU(cudaMemcpyAsync(o.accepts_out, a_d, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
   if (st_host || e_host || b_host || a_host || (init && init_d != init)) {
     QP_CU(cudaStreamSynchronize(st));
-    if (dense_launched) {
+    if (err_armed) {
       int32_t err = 0;
-      QP_CU(cudaMemcpy(&err, h->dense_err.p, 4, cudaMemcpyDeviceToHost));
+      QP_CU(cudaMemcpy(&err, h->kernel_err.p, 4, cudaMemcpyDeviceToHost));
       if (err) return fail(QP_ETIMEOUT, "a bulk row copy of the dense sweep did not complete; "
                                         "the affected replicas report energy INT64_MIN");
     }

@@ -291,41 +291,6 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32)
 // spins (bitset, shared) and, for path QUBOs, the row/column sums that decide
 // feasibility.  dE_k = (1 - 2x_k) h_k; an accepted flip of k streams row k of S
 // (= column k, S is symmetric) with 16-byte loads into h.
-// ---- bulk copies of S rows into shared memory (dense kernel)
-constexpr long long kBulkWaitCycles = 1000000000LL;  // ~0.5 s at 2 GHz, then give up
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// One thread asks for `bytes` (a multiple of 16, both addresses 16-byte
-// aligned) from global `src` into shared `dst`; the copy engine counts the
-// bytes on the mbarrier.  The proxy fence orders the warp's earlier reads of
-// dst before the asynchronous write.
-__device__ __forceinline__ void bulk_row_issue(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar)
-               : "memory");
-}
-
-// Wait for phase `parity` of the mbarrier, giving up after kBulkWaitCycles.
-__device__ __forceinline__ bool bulk_wait(uint32_t mbar, uint32_t parity) {
-  const long long t0 = clock64();
-  while (true) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (clock64() - t0 > kBulkWaitCycles) return false;
-  }
-}
-
 // h += dlt * row, the row already staged in shared memory.
 template <typename ST>
 __device__ __forceinline__ void add_row_staged(int32_t *h, const ST *stage, int np, int dlt, int lane) {
@@ -430,7 +395,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_sweep_dense(const Dens
   unsigned char *wp = p + warp * per_warp;
   int32_t *h = H_SMEM ? reinterpret_cast<int32_t *>(wp) : nullptr;
   ST *stage = BULK ? reinterpret_cast<ST *>(wp + (H_SMEM ? 4 * (size_t)np : 0)) : nullptr;
-  const uint32_t mbar = BULK ? smem_addr(wp + (H_SMEM ? 4 * (size_t)np : 0) + sizeof(ST) * (size_t)np) : 0u;
+  const uint32_t mbar = BULK ? dev::smem_addr(wp + (H_SMEM ? 4 * (size_t)np : 0) + sizeof(ST) * (size_t)np) : 0u;
   uint32_t parity = 0;
   uint32_t *st = reinterpret_cast<uint32_t *>(wp + (H_SMEM ? 4 * (size_t)np : 0) + stage_bytes);
   int16_t *rowsum = reinterpret_cast<int16_t *>(st + nw_pad);
@@ -442,8 +407,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_sweep_dense(const Dens
   const uint32_t rg = (uint32_t)(a.rep_offset + r);
   if (BULK) {
     if (lane == 0) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      dev::mbar_init1(mbar);
+      dev::mbar_init_fence();
     }
     __syncwarp();
   }
@@ -568,14 +533,14 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_sweep_dense(const Dens
         int32_t skk;
         if (BULK) {
           __syncwarp();
-          if (lane == 0) bulk_row_issue(smem_addr(stage), S + (size_t)k * np, (uint32_t)(sizeof(ST) * np), mbar);
-          const bool done = __all_sync(kFull, bulk_wait(mbar, parity));
+          if (lane == 0) dev::bulk_copy(dev::smem_addr(stage), S + (size_t)k * np, (uint32_t)(sizeof(ST) * np), mbar);
+          const bool done = __all_sync(kFull, dev::mbar_wait_bounded(mbar, parity));
           parity ^= 1u;
           if (!done) {
             // the copy did not complete: flag it, let it land (bounded), drop this chain
             if (lane == 0) {
               if (a.err) atomicExch(a.err, 1);
-              bulk_wait(mbar, parity ^ 1u);
+              dev::mbar_wait_bounded(mbar, parity ^ 1u);
               a.E_out[r] = LLONG_MIN;
             }
             return;
