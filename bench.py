@@ -447,8 +447,19 @@ def run_ours(args):
     ann_ms = statistics.mean(anneal_ms)
     achieved_tops = OPS_PER_ATTEMPT * attempts / (ann_ms / 1e3) / 1e12
     traffic = recorded_traffic("rows")
+    # the bytes-per-flip view: each row's field is one C-entry d row (int32 in
+    # shared memory for this field) for its C-1 proposals; the threshold table
+    # is read only for proposals inside the table (not counted)
+    bpa = 4.0 * C / (C - 1)
+    achieved_gbs = bpa * attempts / (statistics.mean(anneal_ms) / 1e3) / 1e9
+    smem_gbs = SMS * 128 * sm_mhz * 1e6 / 1e9
+    bytes_view = {"bytes_per_attempt": bpa, "achieved_GBps": achieved_gbs,
+                  "frac_of_shared_memory_bw": achieved_gbs / smem_gbs,
+                  "frac_of_measured_hbm": achieved_gbs / pk["hbm_gbs"] if pk.get("hbm_gbs") else None,
+                  "note": "d rows come from shared memory (staged once per CTA); DRAM traffic per launch is "
+                          "the 'traffic' figure; the sweep is bound by its dependent instruction chain"}
     roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
-                "frac": achieved_tops / peak_tops, "traffic": traffic,
+                "frac": achieved_tops / peak_tops, "traffic": traffic, "bytes_per_flip": bytes_view,
                 "kernel": "k_sweep_rows" if args.structured_kernel == "rows" else "k_sweep_structured",
                 "kernel_ms": ann_ms,
                 "note": (f"int32 ops: {OPS_PER_ATTEMPT} algorithmic ops per flip attempt x attempts / kernel time; "
