@@ -409,6 +409,15 @@ qp_status qp_ws_decode(const float *logits, int32_t ld, int32_t C, int32_t start
 qp_status qp_ws_decode_walk(const float *logits, int32_t ld, int32_t C, int32_t start_cell, const int32_t *d,
                             uint8_t *state_out, int32_t *path_out);
 
+/* The whole inference step of the warm start for one field: its features
+ * (qp_ws_features), the network's logits (qp_ws_forward) and a feasible seed
+ * decoded from them -- the guided walk (qp_ws_decode_walk) when d (the
+ * field's C x C distance matrix, host, e.g. qp_export_dist) is given, greedy
+ * matching (qp_ws_decode) when d is NULL.  state_out: C*C bytes, path_out: C
+ * int32 (host; either may be NULL).  QP_ERANGE above 256 cells. */
+qp_status qp_ws_infer(qp_ws *ws, const qp_field *field, const int32_t *d, uint8_t *state_out, int32_t *path_out,
+                      void *cuda_stream);
+
 /* Free a handle and its device memory (NULL is ignored). */
 void qp_destroy(qp_handle *h);
 

@@ -533,3 +533,23 @@ extern "C" qp_status qp_ws_decode_walk(const float *logits, int32_t ld, int32_t 
   if (path_out) std::memcpy(path_out, path.data(), (size_t)C * 4);
   return QP_OK;
 }
+
+// ----------------------------------------------------------------------------- one-call inference
+extern "C" qp_status qp_ws_infer(qp_ws *m, const qp_field *field, const int32_t *d, uint8_t *state_out,
+                                 int32_t *path_out, void *stream) {
+  if (!m || !field || (!state_out && !path_out)) return set_error(QP_EINVAL, "bad argument");
+  int32_t C = 0;
+  qp_status s = qp_ws_features(field, nullptr, &C);
+  if (s != QP_OK) return s;
+  if (C < 1 || C > kOut) return set_error(QP_ERANGE, "the field has more cells than the network has steps");
+  std::vector<float> feats((size_t)C * kIn), logits((size_t)C * kOut);
+  s = qp_ws_features(field, feats.data(), nullptr);
+  if (s != QP_OK) return s;
+  s = qp_ws_forward(m, feats.data(), C, logits.data(), stream);
+  if (s != QP_OK) return s;
+  // the start cell's id: free cells before it in row-major order
+  int start = 0;
+  for (int g = 0; g < field->start; ++g) start += !field->free_mask || field->free_mask[g] != 0;
+  return d ? qp_ws_decode_walk(logits.data(), kOut, C, start, d, state_out, path_out)
+           : qp_ws_decode(logits.data(), kOut, C, start, state_out, path_out);
+}

@@ -31,7 +31,7 @@ SYMBOLS = ["qp_build_qubo", "qp_build_from_dense", "qp_qubo_info", "qp_export_de
            "qp_batch_run", "qp_batch_info", "qp_batch_destroy", "qp_anneal_batch", "qp_decode_path",
            "qp_decode_batch", "qp_repair_batch", "qp_repair_path", "qp_anneal_timed", "qp_anneal_pt", "qp_ws_create", "qp_ws_destroy", "qp_ws_param_count", "qp_ws_get_params",
            "qp_ws_set_params", "qp_ws_features", "qp_ws_forward", "qp_ws_grads", "qp_ws_train_step",
-           "qp_ws_decode", "qp_ws_decode_walk", "qp_destroy", "qp_last_error"]
+           "qp_ws_decode", "qp_ws_decode_walk", "qp_ws_infer", "qp_destroy", "qp_last_error"]
 
 
 class QpError(RuntimeError):
@@ -112,6 +112,7 @@ def lib():
                 "qp_ws_train_step": [vp, vp, vp, vp, i32, ct.c_float, vp, vp],
                 "qp_ws_decode": [vp, i32, i32, i32, vp, vp],
                 "qp_ws_decode_walk": [vp, i32, i32, i32, vp, vp, vp],
+                "qp_ws_infer": [vp, P(qp_field), vp, vp, vp, vp],
                 "qp_decode_path": [vp, vp, vp, vp],
                 "qp_decode_batch": [vp, i32, vp, vp, vp, vp],
                 "qp_repair_batch": [vp, i32, vp, i32, vp, vp, vp, vp],
@@ -492,4 +493,18 @@ def qp_ws_decode_walk(logits, C, start_cell, d):
     st = np.zeros(C * C, np.uint8)
     path = np.zeros(C, np.int32)
     _check(lib().qp_ws_decode_walk(_ptr(L), L.shape[1], int(C), int(start_cell), _ptr(dd), _ptr(st), _ptr(path)))
+    return st, path
+
+
+def qp_ws_infer(m: WarmStartModel, field, d=None, stream=None):
+    """-> (state uint8 [C*C], path int32 [C]): features, logits and the decoded
+    seed of one field in one call (guided walk when d is given, else greedy
+    matching)."""
+    mask = None if field.free_mask is None else np.ascontiguousarray(field.free_mask, np.uint8)
+    f = qp_field(int(field.rows), int(field.cols), None if mask is None else mask.ctypes.data, int(field.start))
+    C = int(mask.sum()) if mask is not None else field.rows * field.cols
+    st = np.zeros(C * C, np.uint8)
+    path = np.zeros(C, np.int32)
+    dd = None if d is None else np.ascontiguousarray(d, np.int32)
+    _check(lib().qp_ws_infer(m.ptr, ct.byref(f), _ptr(dd), _ptr(st), _ptr(path), _stream(stream)))
     return st, path

@@ -105,14 +105,11 @@ def learned_seed(model, field, handle, decode="walk", d=None):
     """-> (state uint8 [C*C], path length) of the decoded network prediction.
     decode = "walk": nearest unvisited cell, ties by the predicted step;
     "match": greedy max-logit matching of cells to steps."""
-    X = qpath.qp_ws_features(field)
-    L = qpath.qp_ws_forward(model, X)
-    C = X.shape[0]
     if decode == "walk":
         d = qpath.qp_export_dist(handle) if d is None else d
-        state, _ = qpath.qp_ws_decode_walk(L, C, start_cell(field), d)
+        state, _ = qpath.qp_ws_infer(model, field, d)
     else:
-        state, _ = qpath.qp_ws_decode(L, C, start_cell(field))
+        state, _ = qpath.qp_ws_infer(model, field, None)
     dec = qpath.qp_decode_path(handle, state)
     return state, dec[1]
 

@@ -90,3 +90,20 @@ def test_training_reduces_loss(dev):
     got = qpath.qp_ws_forward(m, X[:256])
     ref, _ = mlp_ref.forward(params, X[:256], bf16_storage=True)
     assert np.abs(got - ref).max() <= 2e-2 * max(1.0, np.abs(ref).max() / 10)
+
+
+def test_infer_equals_the_three_steps(dev):
+    """qp_ws_infer = features, forward and decode, for both decoders; the seed
+    is a feasible one-hot state with the start cell at step 0."""
+    m = qpath.WarmStartModel(seed=5)
+    f = inputs.obstacles(9, 11, 0.15, seed=4, start=7)
+    h = qpath.qp_build_qubo(f)
+    C = h.info["C"]
+    d = qpath.qp_export_dist(h)
+    L = qpath.qp_ws_forward(m, qpath.qp_ws_features(f))
+    start = int(np.cumsum(f.free_mask)[f.start] - 1)
+    for dd, ref in ((d, qpath.qp_ws_decode_walk(L, C, start, d)), (None, qpath.qp_ws_decode(L, C, start))):
+        st, path = qpath.qp_ws_infer(m, f, dd)
+        assert (st == ref[0]).all() and (path == ref[1]).all()
+        assert path[0] == start and sorted(path.tolist()) == list(range(C))
+        assert qpath.qp_decode_path(h, st) is not None
