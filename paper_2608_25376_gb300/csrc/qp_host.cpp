@@ -673,9 +673,9 @@ extern "C" qp_status qp_anneal_pt(qp_handle *h, int32_t G, const qp_pt_schedule 
   cudaStream_t st = static_cast<cudaStream_t>(stream_);
   DeviceSchedule lt;
   QP_TRY(device_schedule(ladder, &lt));
-  const uint32_t *xthr;
-  const int64_t *xoff;
-  const int32_t *xlen;
+  const uint32_t *xthr = nullptr;
+  const int64_t *xoff = nullptr;
+  const int32_t *xlen = nullptr;
   QP_TRY(exchange_tables(ladder, &xthr, &xoff, &xlen));
   const size_t n = (size_t)h->n;
   QP_TRY(h->pt_states[0].ensure((size_t)R * n));

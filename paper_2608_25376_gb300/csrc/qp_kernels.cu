@@ -320,7 +320,7 @@ __device__ __forceinline__ void add_row_staged(int32_t *h, const ST *stage, int 
 
 template <typename ST>
 __device__ __forceinline__ void add_row(int32_t *h, const ST *row, int np, int dlt, int lane) {
-  if (sizeof(ST) == 2) {
+  if constexpr (sizeof(ST) == 2) {
     // 8 loads of 16 bytes in flight per lane (4 KB per warp) before any use
     constexpr int MLP = 8;
     for (int c0 = lane * 8; c0 < np; c0 += 256 * MLP) {
@@ -345,30 +345,30 @@ __device__ __forceinline__ void add_row(int32_t *h, const ST *row, int np, int d
         }
       }
     }
-    return;
-  }
-  for (int c0 = lane * 8; c0 < np; c0 += 1024) {
-    int v[4][8];
+  } else {
+    for (int c0 = lane * 8; c0 < np; c0 += 1024) {
+      int v[4][8];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int c = c0 + b * 256;
-      if (c < np) {
-        const int4 q0 = __ldg(reinterpret_cast<const int4 *>(row + c));
-        const int4 q1 = __ldg(reinterpret_cast<const int4 *>(row + c) + 1);
-        v[b][0] = q0.x; v[b][1] = q0.y; v[b][2] = q0.z; v[b][3] = q0.w;
-        v[b][4] = q1.x; v[b][5] = q1.y; v[b][6] = q1.z; v[b][7] = q1.w;
+      for (int b = 0; b < 4; ++b) {
+        const int c = c0 + b * 256;
+        if (c < np) {
+          const int4 q0 = __ldg(reinterpret_cast<const int4 *>(row + c));
+          const int4 q1 = __ldg(reinterpret_cast<const int4 *>(row + c) + 1);
+          v[b][0] = q0.x; v[b][1] = q0.y; v[b][2] = q0.z; v[b][3] = q0.w;
+          v[b][4] = q1.x; v[b][5] = q1.y; v[b][6] = q1.z; v[b][7] = q1.w;
+        }
       }
-    }
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int c = c0 + b * 256;
-      if (c < np) {
-        int4 *hp = reinterpret_cast<int4 *>(h + c);
-        int4 a0 = hp[0], a1 = hp[1];
-        a0.x += dlt * v[b][0]; a0.y += dlt * v[b][1]; a0.z += dlt * v[b][2]; a0.w += dlt * v[b][3];
-        a1.x += dlt * v[b][4]; a1.y += dlt * v[b][5]; a1.z += dlt * v[b][6]; a1.w += dlt * v[b][7];
-        hp[0] = a0;
-        hp[1] = a1;
+      for (int b = 0; b < 4; ++b) {
+        const int c = c0 + b * 256;
+        if (c < np) {
+          int4 *hp = reinterpret_cast<int4 *>(h + c);
+          int4 a0 = hp[0], a1 = hp[1];
+          a0.x += dlt * v[b][0]; a0.y += dlt * v[b][1]; a0.z += dlt * v[b][2]; a0.w += dlt * v[b][3];
+          a1.x += dlt * v[b][4]; a1.y += dlt * v[b][5]; a1.z += dlt * v[b][6]; a1.w += dlt * v[b][7];
+          hp[0] = a0;
+          hp[1] = a1;
+        }
       }
     }
   }
