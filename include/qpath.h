@@ -418,6 +418,13 @@ qp_status qp_ws_decode_walk(const float *logits, int32_t ld, int32_t C, int32_t 
 qp_status qp_ws_infer(qp_ws *ws, const qp_field *field, const int32_t *d, uint8_t *state_out, int32_t *path_out,
                       void *cuda_stream);
 
+/* Self-test of the bounded wait that guards the library's asynchronous copies
+ * (no counterpart in the paper): one warp waits on an mbarrier phase that
+ * nothing completes.  *timed_out = 1 when the wait gave up after its bound
+ * (~0.5 s of SM clock) instead of hanging; *waited_ms (NULL allowed) = how
+ * long it waited, from the SM clock.  The context stays usable. */
+qp_status qp_selftest_wait(int32_t *timed_out, double *waited_ms);
+
 /* Free a handle and its device memory (NULL is ignored). */
 void qp_destroy(qp_handle *h);
 
