@@ -18,12 +18,15 @@
 #include <tuple>
 #include <vector>
 
-#include "qp_internal.h"
+#include "qp_host.h"
 
 using namespace qp;
+using namespace qp::host;
 
 // --------------------------------------------------------------------------- errors
-namespace {
+namespace qp {
+namespace host {
+
 thread_local std::string g_err;
 
 qp_status fail(qp_status s, const char *fmt, ...) {
@@ -36,22 +39,6 @@ qp_status fail(qp_status s, const char *fmt, ...) {
   return s;
 }
 
-#define QP_CU(call)                                                                    \
-  do {                                                                                 \
-    cudaError_t e_ = (call);                                                           \
-    if (e_ != cudaSuccess)                                                             \
-      return fail(e_ == cudaErrorMemoryAllocation ? QP_ENOMEM : QP_ECUDA, "%s: %s (%s:%d)", \
-                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                  \
-  } while (0)
-
-#define QP_TRY(expr)              \
-  do {                            \
-    qp_status s_ = (expr);        \
-    if (s_ != QP_OK) return s_;   \
-  } while (0)
-
-int round_up_i(int x, int m) { return (x + m - 1) / m * m; }
-
 bool is_device_ptr(const void *p) {
   if (!p) return false;
   cudaPointerAttributes at;
@@ -62,31 +49,12 @@ bool is_device_ptr(const void *p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// A device allocation owned by a handle, grown on demand.
-struct DevBuf {
-  void *p = nullptr;
-  size_t bytes = 0;
-  ~DevBuf() { release(); }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
-  }
-  qp_status ensure(size_t want) {
-    if (want <= bytes) return QP_OK;
-    release();
-    cudaError_t e = cudaMalloc(&p, want);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      p = nullptr;
-      return fail(QP_ENOMEM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
-    }
-    bytes = want;
-    return QP_OK;
-  }
-  template <typename T>
-  T *as() const { return static_cast<T *>(p); }
-};
+}  // namespace host
+}  // namespace qp
+
+namespace {
+
+int round_up_i(int x, int m) { return (x + m - 1) / m * m; }
 
 // Exact round(scale * sqrt(q)): r = floor(sqrt(N)) for N = scale^2 q by a
 // floating-point estimate corrected in integers, then round half up, which
@@ -99,7 +67,12 @@ int64_t round_scaled_sqrt(int64_t q, int64_t scale) {
   return (N - r * r > r) ? r + 1 : r;
 }
 
+}  // namespace
+
 // --------------------------------------------------------------------------- schedules
+namespace qp {
+namespace host {
+
 double temperature(const qp_schedule &sc, int s) {
   if (sc.n_sweeps <= 1) return sc.T0;
   return sc.T0 * std::pow(sc.T1 / sc.T0, (double)s / (double)(sc.n_sweeps - 1));
@@ -127,15 +100,7 @@ qp_status check_schedule(const qp_schedule *sc) {
   return QP_OK;
 }
 
-struct SchedKey {
-  int dev;
-  int32_t n;
-  uint64_t t0, t1;
-  bool operator<(const SchedKey &o) const {
-    return std::tie(dev, n, t0, t1) < std::tie(o.dev, o.n, o.t0, o.t1);
-  }
-};
-
+namespace {
 struct SchedEntry {
   DevBuf thr, off, len, c;
   DeviceSchedule view;
@@ -143,6 +108,7 @@ struct SchedEntry {
 
 std::mutex g_sched_mu;
 std::map<SchedKey, std::unique_ptr<SchedEntry>> g_sched;
+}  // namespace
 
 // Device tables of a schedule (all n_sweeps sweeps), built once per device and
 // kept until the process exits.
@@ -219,31 +185,8 @@ qp_status device_schedule(const qp_schedule &sc, DeviceSchedule *out) {
   return QP_OK;
 }
 
-}  // namespace
-
-// --------------------------------------------------------------------------- the handle
-struct qp_handle {
-  int dev = 0;
-  bool path = false;       // built from a field (structured terms available)
-  int32_t C = 0, start = 0, A = 0, B = 0, max_d = 0;
-  int64_t n = 0, c0 = 0;
-  std::vector<int32_t> d;  // C x C (host)
-  // device data
-  DevBuf d_dev;            // C x Cp, int16 or int32
-  bool d_i16 = false;
-  int32_t Cp = 0;
-  DevBuf d32_dev;          // C x C int32 (decode, dense build)
-  DevBuf S_dev;            // n x np, int16 or int32
-  bool has_dense = false, S_i16 = false;
-  int32_t np = 0;
-  DevBuf frozen_bits, fval_bits;
-  std::vector<uint8_t> frozen_host, fval_host;  // generic QUBOs
-  // scratch
-  DevBuf gstate, hbuf, in_stage, st_stage, e_stage, b_stage, a_stage, p_stage, l_stage, r_stage;
-  DevBuf kernel_err;  // int32 flag: a bulk row copy of the dense sweep did not complete
-  DevBuf t_states[2], t_E, t_paths, t_len, t_stat;  // qp_anneal_timed
-  DevBuf pt_states[2], pt_E, pt_bseg, pt_best, pt_level, pt_owner, pt_swaps;  // qp_anneal_pt
-};
+}  // namespace host
+}  // namespace qp
 
 namespace {
 
@@ -260,20 +203,6 @@ qp_status upload_bits(qp_handle *h, const std::vector<uint8_t> &fr, const std::v
   QP_CU(cudaMemcpy(h->fval_bits.p, vb.data(), nw * 4, cudaMemcpyHostToDevice));
   return QP_OK;
 }
-
-struct DevSet {
-  int prev = -1;
-  explicit DevSet(int dev) {
-    int cur = 0;
-    if (cudaGetDevice(&cur) == cudaSuccess && cur != dev) {
-      prev = cur;
-      cudaSetDevice(dev);
-    }
-  }
-  ~DevSet() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
 
 }  // namespace
 
@@ -461,7 +390,8 @@ extern "C" qp_status qp_thresholds(const qp_schedule *sc, int32_t sweep, uint32_
 }
 
 // --------------------------------------------------------------------------- anneal
-namespace {
+namespace qp {
+namespace host {
 
 // The structured sweep of a.R replicas: the row kernel when allowed and the
 // field fits it, else the flat kernel (spins in global memory when a
@@ -487,7 +417,8 @@ qp_status launch_structured_auto(qp_handle *h, StructArgs &a, int W, bool allow_
   return QP_OK;
 }
 
-}  // namespace
+}  // namespace host
+}  // namespace qp
 
 extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc, uint64_t seed,
                                   const uint8_t *init, uint8_t *states_out, int64_t *energies_out,
@@ -602,152 +533,6 @@ extern "C" qp_status qp_anneal(qp_handle *h, int32_t R, const qp_schedule *sc, u
   return qp_anneal_ex(h, R, sc, seed, init, states_out, energies_out, best_out, nullptr, stream);
 }
 
-// --------------------------------------------------------------------------- replica exchange
-namespace {
-
-struct XchgEntry {
-  DevBuf thr, off, len;
-};
-std::mutex g_xchg_mu;
-std::map<SchedKey, std::unique_ptr<XchgEntry>> g_xchg;
-
-// Exchange tables of a ladder: row m (m < M-1) holds the Metropolis
-// thresholds at T_m T_{m+1} / (T_{m+1} - T_m); built once per device.
-qp_status exchange_tables(const qp_schedule &ladder, const uint32_t **thr, const int64_t **off,
-                          const int32_t **len) {
-  int dev = 0;
-  QP_CU(cudaGetDevice(&dev));
-  SchedKey key{dev, ladder.n_sweeps, 0, 0};
-  std::memcpy(&key.t0, &ladder.T0, 8);
-  std::memcpy(&key.t1, &ladder.T1, 8);
-  std::lock_guard<std::mutex> lk(g_xchg_mu);
-  auto it = g_xchg.find(key);
-  if (it == g_xchg.end()) {
-    const int M = ladder.n_sweeps;
-    std::vector<int64_t> o(M - 1);
-    std::vector<int32_t> l(M - 1);
-    std::vector<uint32_t> all, tab;
-    for (int m = 0; m + 1 < M; ++m) {
-      const double Tm = temperature(ladder, m), Tn = temperature(ladder, m + 1);
-      const double Te = Tm * Tn / (Tn - Tm);
-      if (!(Te > 0.0) || !std::isfinite(Te) || Te > 1e8)
-        return fail(QP_ERANGE, "ladder levels %d and %d are too close (exchange temperature %g)", m, m + 1, Te);
-      build_thresholds(Te, tab);
-      o[m] = (int64_t)all.size();
-      l[m] = (int32_t)tab.size();
-      all.insert(all.end(), tab.begin(), tab.end());
-    }
-    auto e = std::make_unique<XchgEntry>();
-    QP_TRY(e->thr.ensure(all.size() * 4));
-    QP_TRY(e->off.ensure(o.size() * 8));
-    QP_TRY(e->len.ensure(l.size() * 4));
-    QP_CU(cudaMemcpy(e->thr.p, all.data(), all.size() * 4, cudaMemcpyHostToDevice));
-    QP_CU(cudaMemcpy(e->off.p, o.data(), o.size() * 8, cudaMemcpyHostToDevice));
-    QP_CU(cudaMemcpy(e->len.p, l.data(), l.size() * 4, cudaMemcpyHostToDevice));
-    it = g_xchg.emplace(key, std::move(e)).first;
-  }
-  *thr = it->second->thr.as<uint32_t>();
-  *off = it->second->off.as<int64_t>();
-  *len = it->second->len.as<int32_t>();
-  return QP_OK;
-}
-
-}  // namespace
-
-extern "C" qp_status qp_anneal_pt(qp_handle *h, int32_t G, const qp_pt_schedule *pt, uint64_t seed,
-                                  const uint8_t *init, uint8_t *states_out, int64_t *energies_out,
-                                  int64_t *best_out, int32_t *levels_out, int64_t *swaps_out, void *stream_) {
-  g_err.clear();
-  if (!h || !pt || !states_out || !energies_out || G < 1) return fail(QP_EINVAL, "bad argument");
-  if (!h->path) return fail(QP_EINVAL, "replica exchange needs a handle built by qp_build_qubo");
-  const int M = pt->levels, I = pt->sweeps_per_exchange, X = pt->exchanges;
-  if (M < 2 || I < 1 || X < 1) return fail(QP_EINVAL, "need levels >= 2, sweeps_per_exchange >= 1, exchanges >= 1");
-  if (!(pt->T_lo > 0.0) || !(pt->T_hi > pt->T_lo) || !std::isfinite(pt->T_hi))
-    return fail(QP_EINVAL, "need 0 < T_lo < T_hi (finite)");
-  if ((int64_t)G * M > INT32_MAX / 2) return fail(QP_ERANGE, "too many chains");
-  if ((int64_t)I * X > INT32_MAX) return fail(QP_ERANGE, "too many sweeps");
-  qp_schedule ladder{M, pt->T_lo, pt->T_hi, 0, M};
-  QP_TRY(check_schedule(&ladder));
-  const int32_t R = G * M;
-  DevSet ds(h->dev);
-  cudaStream_t st = static_cast<cudaStream_t>(stream_);
-  DeviceSchedule lt;
-  QP_TRY(device_schedule(ladder, &lt));
-  const uint32_t *xthr = nullptr;
-  const int64_t *xoff = nullptr;
-  const int32_t *xlen = nullptr;
-  QP_TRY(exchange_tables(ladder, &xthr, &xoff, &xlen));
-  const size_t n = (size_t)h->n;
-  QP_TRY(h->pt_states[0].ensure((size_t)R * n));
-  QP_TRY(h->pt_states[1].ensure((size_t)R * n));
-  QP_TRY(h->pt_E.ensure((size_t)R * 8));
-  QP_TRY(h->pt_bseg.ensure((size_t)R * 8));
-  QP_TRY(h->pt_best.ensure((size_t)R * 8));
-  QP_TRY(h->pt_level.ensure((size_t)R * 4));
-  QP_TRY(h->pt_owner.ensure((size_t)R * 4));
-  QP_TRY(h->pt_swaps.ensure((size_t)G * (M - 1) * 8));
-  {
-    std::vector<int32_t> lev(R), own(R);
-    std::vector<int64_t> best(R, INT64_MAX);
-    for (int r = 0; r < R; ++r) {
-      lev[r] = r % M;
-      own[r] = r;
-    }
-    QP_CU(cudaMemcpyAsync(h->pt_level.p, lev.data(), (size_t)R * 4, cudaMemcpyHostToDevice, st));
-    QP_CU(cudaMemcpyAsync(h->pt_owner.p, own.data(), (size_t)R * 4, cudaMemcpyHostToDevice, st));
-    QP_CU(cudaMemcpyAsync(h->pt_best.p, best.data(), (size_t)R * 8, cudaMemcpyHostToDevice, st));
-    QP_CU(cudaMemsetAsync(h->pt_swaps.p, 0, (size_t)G * (M - 1) * 8, st));
-    QP_CU(cudaStreamSynchronize(st));  // the host vectors go out of scope
-  }
-  const uint8_t *init_d = init;
-  if (init && !is_device_ptr(init)) {
-    QP_TRY(h->in_stage.ensure((size_t)R * n));
-    QP_CU(cudaMemcpyAsync(h->in_stage.p, init, (size_t)R * n, cudaMemcpyHostToDevice, st));
-    init_d = h->in_stage.as<uint8_t>();
-  }
-  uint8_t *cur = h->pt_states[0].as<uint8_t>(), *nxt = h->pt_states[1].as<uint8_t>();
-  StructArgs a{};
-  a.C = h->C; a.Cp = h->Cp; a.start = h->start; a.A = h->A; a.B = h->B;
-  a.d = h->d_dev.p;
-  a.R = R; a.rep_offset = 0;
-  a.key0 = (uint32_t)seed; a.key1 = (uint32_t)(seed >> 32);
-  a.thr = lt.thr; a.thr_off = lt.off; a.thr_len = lt.len; a.thr_c = lt.c;
-  a.E_out = h->pt_E.as<int64_t>(); a.best_out = h->pt_bseg.as<int64_t>(); a.acc_out = nullptr;
-  a.level = h->pt_level.as<int32_t>();
-  PtArgs x{};
-  x.G = G; x.M = M;
-  x.E = h->pt_E.as<int64_t>(); x.best_seg = h->pt_bseg.as<int64_t>(); x.best = h->pt_best.as<int64_t>();
-  x.owner = h->pt_owner.as<int32_t>(); x.level = h->pt_level.as<int32_t>(); x.swaps = h->pt_swaps.as<int64_t>();
-  x.thr = xthr; x.off = xoff; x.len = xlen;
-  x.key0 = a.key0; x.key1 = a.key1;
-  LaunchInfo info;
-  for (int e = 0; e < X; ++e) {
-    a.sweep_begin = e * I;
-    a.sweep_end = (e + 1) * I;
-    a.init = e == 0 ? init_d : cur;
-    a.states_out = nxt;
-    QP_TRY(launch_structured_auto(h, a, 4, true, st, &info));
-    x.phase = e & 1;
-    x.round = e;
-    QP_CU(launch_pt_exchange(x, st));
-    std::swap(cur, nxt);
-  }
-  bool host_out = false;
-  auto put = [&](void *dst, const void *src, size_t bytes) -> qp_status {
-    if (!dst) return QP_OK;
-    host_out = host_out || !is_device_ptr(dst);
-    QP_CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
-    return QP_OK;
-  };
-  QP_TRY(put(states_out, cur, (size_t)R * n));
-  QP_TRY(put(energies_out, h->pt_E.p, (size_t)R * 8));
-  QP_TRY(put(best_out, h->pt_best.p, (size_t)R * 8));
-  QP_TRY(put(levels_out, h->pt_level.p, (size_t)R * 4));
-  QP_TRY(put(swaps_out, h->pt_swaps.p, (size_t)G * (M - 1) * 8));
-  if (host_out || (init && init_d != init)) QP_CU(cudaStreamSynchronize(st));
-  return QP_OK;
-}
-
 // --------------------------------------------------------------------------- decode
 extern "C" qp_status qp_decode_path(const qp_handle *h, const uint8_t *state, int32_t *path_out,
                                     int64_t *length_out) {
@@ -812,198 +597,6 @@ extern "C" qp_status qp_decode_batch(const qp_handle *hc, int32_t R, const uint8
   return QP_OK;
 }
 
-extern "C" qp_status qp_repair_batch(const qp_handle *hc, int32_t R, const uint8_t *states, int32_t max_passes,
-                                     int32_t *paths_out, int64_t *lengths_out, int32_t *status_out,
-                                     void *stream_) {
-  g_err.clear();
-  qp_handle *h = const_cast<qp_handle *>(hc);
-  if (!h || !states || !paths_out || !lengths_out || R < 1) return fail(QP_EINVAL, "bad argument");
-  if (!h->path) return fail(QP_EINVAL, "a generic QUBO has no path");
-  DevSet ds(h->dev);
-  cudaStream_t st = static_cast<cudaStream_t>(stream_);
-  const size_t n = (size_t)h->n;
-  const uint8_t *sd = states;
-  bool sync = false;
-  if (!is_device_ptr(states)) {
-    QP_TRY(h->in_stage.ensure((size_t)R * n));
-    QP_CU(cudaMemcpyAsync(h->in_stage.p, states, (size_t)R * n, cudaMemcpyHostToDevice, st));
-    sd = h->in_stage.as<uint8_t>();
-    sync = true;
-  }
-  int32_t *pd = paths_out, *rd = status_out;
-  int64_t *ld = lengths_out;
-  const bool ph = !is_device_ptr(paths_out), lh = !is_device_ptr(lengths_out);
-  const bool rh = status_out && !is_device_ptr(status_out);
-  if (ph) { QP_TRY(h->p_stage.ensure((size_t)R * h->C * 4)); pd = h->p_stage.as<int32_t>(); }
-  if (lh) { QP_TRY(h->l_stage.ensure((size_t)R * 8)); ld = h->l_stage.as<int64_t>(); }
-  if (!status_out || rh) { QP_TRY(h->r_stage.ensure((size_t)R * 4)); rd = h->r_stage.as<int32_t>(); }
-  QP_CU(launch_repair(sd, R, h->C, h->start, h->d32_dev.as<int32_t>(), max_passes, pd, ld, rd, st));
-  if (ph) QP_CU(cudaMemcpyAsync(paths_out, pd, (size_t)R * h->C * 4, cudaMemcpyDeviceToHost, st));
-  if (lh) QP_CU(cudaMemcpyAsync(lengths_out, ld, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
-  if (rh) QP_CU(cudaMemcpyAsync(status_out, rd, (size_t)R * 4, cudaMemcpyDeviceToHost, st));
-  if (sync || ph || lh || rh) QP_CU(cudaStreamSynchronize(st));
-  return QP_OK;
-}
-
-extern "C" qp_status qp_repair_path(const qp_handle *h, const uint8_t *state, int32_t max_passes,
-                                    int32_t *path_out, int64_t *length_out, int32_t *status_out) {
-  if (!path_out || !length_out || is_device_ptr(path_out) || is_device_ptr(length_out) ||
-      (status_out && is_device_ptr(status_out)))
-    return fail(QP_EINVAL, "qp_repair_path: outputs must be host memory");
-  int32_t status = 0;
-  QP_TRY(qp_repair_batch(h, 1, state, max_passes, path_out, length_out, &status, nullptr));
-  if (status_out) *status_out = status;
-  return QP_OK;
-}
-
-namespace {
-
-double ms_since(const std::chrono::steady_clock::time_point &t0) {
-  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-}
-
-// n rounded down to m * 2^e with 8 <= m < 16 (n itself below 16), so that
-// budget-fitted schedules come from a short list and their tables are reused.
-int32_t quantize_sweeps(int64_t n) {
-  if (n < 16) return (int32_t)std::max<int64_t>(1, n);
-  int e = 0;
-  while ((n >> e) >= 16) ++e;
-  return (int32_t)((n >> e) << e);
-}
-
-}  // namespace
-
-extern "C" qp_status qp_anneal_timed(qp_handle *h, int32_t R, const qp_schedule *sc, uint64_t seed,
-                                     double time_limit_ms, int32_t max_passes, int32_t *path_out,
-                                     int64_t *length_out, uint8_t *state_out, qp_timed_info *info,
-                                     void *stream_) {
-  const auto t0 = std::chrono::steady_clock::now();
-  g_err.clear();
-  if (!h || !sc || !path_out || !length_out || R < 1) return fail(QP_EINVAL, "bad argument");
-  if (!h->path) return fail(QP_EINVAL, "qp_anneal_timed needs a handle built by qp_build_qubo");
-  if (!(time_limit_ms > 0.0) || !std::isfinite(time_limit_ms)) return fail(QP_EINVAL, "time_limit_ms must be > 0");
-  qp_schedule full = *sc;
-  full.sweep_begin = 0;
-  full.sweep_end = full.n_sweeps;
-  QP_TRY(check_schedule(&full));
-  if ((int64_t)R * 2 > INT32_MAX) return fail(QP_ERANGE, "too many replicas");
-  DevSet ds(h->dev);
-  cudaStream_t st = static_cast<cudaStream_t>(stream_);
-  const size_t n = (size_t)h->n;
-  const int C = h->C;
-  QP_TRY(h->t_states[0].ensure((size_t)R * n));
-  QP_TRY(h->t_states[1].ensure((size_t)R * n));
-  QP_TRY(h->t_E.ensure((size_t)R * 8));
-  QP_TRY(h->t_paths.ensure((size_t)R * C * 4));
-  QP_TRY(h->t_len.ensure((size_t)R * 8));
-  QP_TRY(h->t_stat.ensure((size_t)R * 4));
-  uint8_t *S0 = h->t_states[0].as<uint8_t>(), *S1 = h->t_states[1].as<uint8_t>();
-  int64_t *E = h->t_E.as<int64_t>(), *Ld = h->t_len.as<int64_t>();
-  int32_t *Pd = h->t_paths.as<int32_t>(), *Sd = h->t_stat.as<int32_t>();
-  DeviceSchedule dsched;
-  QP_TRY(device_schedule(full, &dsched));
-
-  std::vector<int64_t> len(R), en(R);
-  std::vector<int32_t> stat(R);
-  struct Best {
-    int64_t length = INT64_MAX, energy = 0;
-    int32_t replica = -1, status = 0;
-  } best;
-  int64_t n_feasible = 0;
-  // Repair the R final states in `S`, fold them into `best` (shortest path,
-  // ties to the smaller replica index) and keep the winner's path and state.
-  auto harvest = [&](const uint8_t *S, int32_t offset) -> qp_status {
-    QP_CU(launch_repair(S, R, C, h->start, h->d32_dev.as<int32_t>(), max_passes, Pd, Ld, Sd, st));
-    QP_CU(cudaMemcpyAsync(len.data(), Ld, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
-    QP_CU(cudaMemcpyAsync(stat.data(), Sd, (size_t)R * 4, cudaMemcpyDeviceToHost, st));
-    QP_CU(cudaMemcpyAsync(en.data(), E, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
-    QP_CU(cudaStreamSynchronize(st));
-    int arg = -1;
-    for (int r = 0; r < R; ++r) {
-      n_feasible += stat[r] != 2;
-      if (len[r] < best.length) {
-        best.length = len[r];
-        arg = r;
-      }
-    }
-    if (arg >= 0) {
-      best.replica = offset + arg;
-      best.status = stat[arg];
-      best.energy = en[arg];
-      QP_CU(cudaMemcpyAsync(path_out, Pd + (size_t)arg * C, (size_t)C * 4, cudaMemcpyDeviceToHost, st));
-      if (state_out) QP_CU(cudaMemcpyAsync(state_out, S + (size_t)arg * n, n, cudaMemcpyDeviceToHost, st));
-      QP_CU(cudaStreamSynchronize(st));
-    }
-    return QP_OK;
-  };
-  auto run = [&](const qp_schedule &s, int32_t b, int32_t e, const uint8_t *init, uint8_t *out,
-                 int32_t offset) -> qp_status {
-    qp_schedule part = s;
-    part.sweep_begin = b;
-    part.sweep_end = e;
-    qp_anneal_opts o{};
-    o.replica_offset = offset;
-    o.flags = QP_ANNEAL_SKIP_SETTLED;  // same results, settled sweeps cost nothing
-    return qp_anneal_ex(h, R, &part, seed, init, out, E, nullptr, &o, st);
-  };
-
-  // Probes: 9 sweeps at the constant temperature T0, then 9 at T1 starting
-  // from the first probe's states; sweeps 1..8 of each are timed (sweep 0 of
-  // the first also pays any first-launch cost).  Hot sweeps are the slowest
-  // and cold ones the fastest; the schedule's time per sweep is taken as the
-  // mean of the two.  The probes' chains are thrown away; their tables are 9
-  // short rows each.
-  auto probe_at = [&](double T, const uint8_t *init, uint8_t *out, double *ms_out) -> qp_status {
-    qp_schedule pr = full;
-    pr.n_sweeps = 9;
-    pr.T0 = pr.T1 = T;
-    pr.sweep_end = 9;
-    QP_TRY(run(pr, 0, 1, init, S1, 0));
-    QP_CU(cudaStreamSynchronize(st));
-    const double ta = ms_since(t0);
-    QP_TRY(run(pr, 1, 9, S1, out, 0));
-    QP_CU(cudaStreamSynchronize(st));
-    *ms_out = (ms_since(t0) - ta) / 8.0;
-    return QP_OK;
-  };
-  double t_hot = 0.0, t_cold = 0.0;
-  QP_TRY(probe_at(full.T0, nullptr, S0, &t_hot));
-  QP_TRY(probe_at(full.T1, S0, S0, &t_cold));
-  const double probe_ms = ms_since(t0);
-  const double per_sweep = std::max(0.5 * (t_hot + t_cold), 1e-6);
-  const double left = time_limit_ms - probe_ms;
-  int32_t n_used = full.n_sweeps;
-  if (per_sweep * full.n_sweeps > 0.9 * left)  // the schedule does not fit: a shorter one that does
-    n_used = std::min(full.n_sweeps, quantize_sweeps((int64_t)std::max(1.0, 0.8 * left / per_sweep)));
-  qp_schedule used = full;
-  used.n_sweeps = n_used;
-  used.sweep_end = n_used;
-  // Rounds of fresh chains (replica indices k*R .. k*R+R-1 in round k); a
-  // round starts while the previous one's duration still fits in what is left.
-  int32_t rounds = 0;
-  double round_ms = 0.0;
-  while ((int64_t)(rounds + 1) * R <= INT32_MAX) {
-    const double now = ms_since(t0);
-    if (rounds > 0 && now + round_ms > time_limit_ms) break;
-    QP_TRY(run(used, 0, n_used, nullptr, S0, rounds * R));
-    QP_TRY(harvest(S0, rounds * R));
-    round_ms = ms_since(t0) - now;
-    ++rounds;
-  }
-  *length_out = best.length;
-  if (info) {
-    info->n_sweeps = n_used;
-    info->rounds = rounds;
-    info->replica = best.replica;
-    info->status = best.status;
-    info->n_feasible = n_feasible;
-    info->energy = best.energy;
-    info->probe_ms = probe_ms;
-    info->elapsed_ms = ms_since(t0);
-  }
-  return QP_OK;
-}
-
 extern "C" void qp_destroy(qp_handle *h) {
   if (!h) return;
   DevSet ds(h->dev);
@@ -1047,137 +640,3 @@ bool device_pointer(const void *p) { return is_device_ptr(p); }
 
 }  // namespace qp
 
-// --------------------------------------------------------------------------- batched anneal
-struct qp_batch {
-  int dev = 0;
-  int count = 0, R = 0, Cmax = 0, W = 0, blocks = 0, n_units = 0;
-  DevBuf fields, units, counter;
-  cudaStream_t cap = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  ~qp_batch() {
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    if (cap) cudaStreamDestroy(cap);
-  }
-};
-
-extern "C" qp_status qp_batch_create(qp_handle *const *hs, int32_t count, int32_t R, const qp_schedule *sc,
-                                     uint64_t seed, uint8_t *const *states_out, int64_t *const *energies_out,
-                                     int64_t *const *best_out, const qp_batch_opts *opts, qp_batch **out) {
-  g_err.clear();
-  if (!hs || !out || !states_out || !energies_out) return fail(QP_EINVAL, "NULL argument");
-  *out = nullptr;
-  if (count < 1 || R < 1) return fail(QP_EINVAL, "need count >= 1 and replicas >= 1");
-  if ((int64_t)count * R > INT32_MAX) return fail(QP_ERANGE, "count x replicas beyond int32");
-  QP_TRY(check_schedule(sc));
-  qp_batch_opts o{};
-  if (opts) o = *opts;
-  auto b = std::make_unique<qp_batch>();
-  QP_CU(cudaGetDevice(&b->dev));
-  int Cmax = 0;
-  for (int f = 0; f < count; ++f) {
-    const qp_handle *h = hs[f];
-    if (!h || !h->path) return fail(QP_EINVAL, "field %d: a batch needs handles built by qp_build_qubo", f);
-    if (h->dev != b->dev) return fail(QP_EINVAL, "field %d lives on another device", f);
-    if (!h->d_i16) return fail(QP_ERANGE, "field %d: a batch needs int16 distances", f);
-    if (!is_device_ptr(states_out[f]) || !is_device_ptr(energies_out[f]) ||
-        (best_out && best_out[f] && !is_device_ptr(best_out[f])))
-      return fail(QP_EINVAL, "field %d: batch outputs must be device memory", f);
-    Cmax = std::max(Cmax, (int)h->C);
-  }
-  int W = o.replicas_per_cta > 0 ? o.replicas_per_cta : 4;
-  while (W > 1 && !batch_supported(Cmax, W)) --W;
-  if (!batch_supported(Cmax, W)) return fail(QP_ERANGE, "largest field (%d cells) too large for the batch kernel", Cmax);
-  DeviceSchedule sched;
-  QP_TRY(device_schedule(*sc, &sched));
-  std::vector<StructArgs> fa(count);
-  for (int f = 0; f < count; ++f) {
-    const qp_handle *h = hs[f];
-    StructArgs &a = fa[f];
-    a = StructArgs{};
-    a.C = h->C; a.Cp = h->Cp; a.start = h->start; a.A = h->A; a.B = h->B;
-    a.d = h->d_dev.p;
-    a.R = R; a.rep_offset = 0;
-    a.sweep_begin = sc->sweep_begin; a.sweep_end = sc->sweep_end;
-    const uint64_t sf = seed + (uint64_t)f;
-    a.key0 = (uint32_t)sf; a.key1 = (uint32_t)(sf >> 32);
-    a.thr = sched.thr; a.thr_off = sched.off; a.thr_len = sched.len; a.thr_c = sched.c;
-    a.init = nullptr;
-    a.states_out = states_out[f]; a.E_out = energies_out[f];
-    a.best_out = best_out ? best_out[f] : nullptr;
-    a.acc_out = nullptr;
-    a.skip_settled = (o.flags & QP_ANNEAL_SKIP_SETTLED) ? 1 : 0;
-  }
-  // work units, largest fields first
-  std::vector<int> order(count);
-  for (int f = 0; f < count; ++f) order[f] = f;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return hs[x]->C > hs[y]->C; });
-  std::vector<int2> units;
-  units.reserve((size_t)count * R);
-  for (int f : order)
-    for (int r = 0; r < R; ++r) units.push_back(make_int2(f, r));
-  QP_TRY(b->fields.ensure(fa.size() * sizeof(StructArgs)));
-  QP_TRY(b->units.ensure(units.size() * sizeof(int2)));
-  QP_TRY(b->counter.ensure(sizeof(int)));
-  QP_CU(cudaMemcpy(b->fields.p, fa.data(), fa.size() * sizeof(StructArgs), cudaMemcpyHostToDevice));
-  QP_CU(cudaMemcpy(b->units.p, units.data(), units.size() * sizeof(int2), cudaMemcpyHostToDevice));
-  int per_sm = 0, sms = 0;
-  QP_CU(batch_prepare(Cmax, W, &per_sm));
-  QP_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev));
-  if (per_sm < 1) return fail(QP_ERANGE, "batch kernel does not fit on an SM");
-  const int want = o.ctas > 0 ? o.ctas : per_sm * sms;
-  b->blocks = std::min(want, (int)((units.size() + W - 1) / W));
-  b->count = count; b->R = R; b->Cmax = Cmax; b->W = W; b->n_units = (int)units.size();
-  // one graph: reset the queue head, run the persistent kernel
-  QP_CU(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
-  QP_CU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e1 = cudaMemsetAsync(b->counter.p, 0, sizeof(int), b->cap);
-  cudaError_t e2 = e1 == cudaSuccess ? launch_batch(b->fields.as<StructArgs>(), b->units.as<int2>(), b->n_units,
-                                                    b->counter.as<int>(), Cmax, W, b->blocks, b->cap)
-                                     : e1;
-  cudaError_t e3 = cudaStreamEndCapture(b->cap, &b->graph);
-  if (e2 != cudaSuccess) return fail(QP_ECUDA, "capturing the batch graph: %s", cudaGetErrorString(e2));
-  if (e3 != cudaSuccess) return fail(QP_ECUDA, "capturing the batch graph: %s", cudaGetErrorString(e3));
-  QP_CU(cudaGraphInstantiate(&b->exec, b->graph, 0));
-  *out = b.release();
-  return QP_OK;
-}
-
-extern "C" qp_status qp_batch_run(qp_batch *b, void *stream) {
-  g_err.clear();
-  if (!b) return fail(QP_EINVAL, "batch is NULL");
-  DevSet ds(b->dev);
-  QP_CU(cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)));
-  return QP_OK;
-}
-
-extern "C" qp_status qp_batch_info(const qp_batch *b, int32_t *replicas_per_cta, int32_t *ctas, int32_t *units) {
-  if (!b) return fail(QP_EINVAL, "batch is NULL");
-  if (replicas_per_cta) *replicas_per_cta = b->W;
-  if (ctas) *ctas = b->blocks;
-  if (units) *units = b->n_units;
-  return QP_OK;
-}
-
-extern "C" void qp_batch_destroy(qp_batch *b) {
-  if (!b) return;
-  DevSet ds(b->dev);
-  delete b;
-}
-
-extern "C" qp_status qp_anneal_batch(qp_handle *const *hs, int32_t count, int32_t R, const qp_schedule *sc,
-                                     uint64_t seed, uint8_t *const *states_out, int64_t *const *energies_out,
-                                     int64_t *const *best_out, void *stream) {
-  qp_batch *b = nullptr;
-  QP_TRY(qp_batch_create(hs, count, R, sc, seed, states_out, energies_out, best_out, nullptr, &b));
-  const qp_status s = qp_batch_run(b, stream);
-  if (s == QP_OK) {
-    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
-    qp_batch_destroy(b);
-    if (e != cudaSuccess) return fail(QP_ECUDA, "batch: %s", cudaGetErrorString(e));
-    return QP_OK;
-  }
-  qp_batch_destroy(b);
-  return s;
-}
