@@ -40,7 +40,9 @@
  *     after the results are in the caller's buffers.
  *   Errors.  Every call returns a status and never aborts; qp_last_error()
  *     gives a message for the calling thread.  Handles are not thread-safe:
- *     use one handle per host thread, or serialise calls on it.
+ *     use one handle per host thread, or serialise calls on it; asynchronous
+ *     calls on one handle must not overlap on the GPU either (different
+ *     streams included), since they share the handle's device buffers.
  */
 #ifndef QPATH_H
 #define QPATH_H
