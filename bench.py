@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--no-other-configs", action="store_true")
     ap.add_argument("--replicas-per-cta", type=int, default=0)
     ap.add_argument("--structured-kernel", default="rows", choices=["rows", "flat"])
-    ap.add_argument("--profile-case", default=None, choices=["rows", "flat", "dense", "mlp"],
+    ap.add_argument("--profile-case", default=None, choices=["rows", "flat", "dense", "mlp", "batch"],
                     help="run one warm-up and one measured launch of that kernel on a sub-range of "
                          "the workload (--sweep-window, --replicas), for ncu captures")
     ap.add_argument("--sweep-window", nargs=2, type=int, default=[0, 100])
@@ -626,6 +626,31 @@ def run_profile_case(args):
     from paper_2608_25376_gb300 import build as qbuild
     qbuild.build()
     from paper_2608_25376_gb300 import inputs, qpath
+    if args.profile_case == "batch":
+        # the batched workload's graph (256 fields x 128 replicas, configuration
+        # 16 replicas per CTA on 152 CTAs) over the sweep window, replayed twice
+        fields = inputs.batch(256, seed=2026)
+        hs = [qpath.qp_build_qubo(f) for f in fields]
+        R = 128
+        a, b = args.sweep_window
+        sc = qpath.schedule(2000, sweep_begin=a, sweep_end=b)
+        st = [torch.zeros((R, h.info["n"]), dtype=torch.uint8, device="cuda") for h in hs]
+        E = [torch.zeros(R, dtype=torch.int64, device="cuda") for _ in hs]
+        B = [torch.zeros(R, dtype=torch.int64, device="cuda") for _ in hs]
+        bt = qpath.qp_batch_create(hs, R, sc, 1, st, E, B, replicas_per_cta=16, ctas=152)
+        times = []
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            bt.run(torch.cuda.current_stream())
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        attempts = sum(R * (b - a) * (h.info["C"] - 1) ** 2 for h in hs)
+        print(json.dumps({"profile_case": "batch", "fields": len(hs), "replicas": R, "sweeps": [a, b], "ms": times,
+                          "attempts": attempts}))
+        bt.close()
+        return 0
     if args.profile_case == "mlp":
         # one warm-up and one measured training step of the warm-start MLP on
         # 16384 cells (64 fields of 256): 11 tensor-core GEMM launches a step
