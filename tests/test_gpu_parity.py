@@ -140,6 +140,36 @@ def test_structured_above_512_cells_falls_back(dev, orc):
     assert_same(gpu_anneal(h, 2, 3, 3), ref)
 
 
+@pytest.mark.parametrize("rows,cols,kernel", [(16, 32, qpath.QP_KERNEL_STRUCTURED_ROWS),
+                                              (16, 32, qpath.QP_KERNEL_STRUCTURED_FLAT),
+                                              (17, 31, qpath.QP_KERNEL_STRUCTURED)])
+def test_structured_at_the_row_kernel_limit(dev, orc, rows, cols, kernel):
+    """C = 512 (the row kernel's widest field: four 128-column chunks per lane,
+    no ragged tail) with both kernels, and C = 527 just past it (the automatic
+    choice falls back to the flat kernel)."""
+    f = inputs.rect(rows, cols, start=rows * cols - 1)
+    P = problem(orc, f)
+    assert P.C == rows * cols
+    h = qpath.qp_build_qubo(f)
+    ref = orc.anneal_structured(P, 3, 4, seed=12, T0=3000.0, T1=2000.0)
+    assert_same(gpu_anneal(h, 3, 4, 12, T0=3000.0, T1=2000.0, kernel=kernel), ref)
+
+
+@pytest.mark.slow
+def test_structured_at_the_cell_limit(dev, orc):
+    """C = 4096, the library's largest field (64 x 64, n = 16.8M variables per
+    replica, spins in global memory): one replica (index 1 of 2), one sweep."""
+    f = inputs.rect(64, 64, start=2080)
+    P = problem(orc, f)
+    assert P.C == 4096
+    h = qpath.qp_build_qubo(f)
+    ref = orc.anneal_structured(P, [1], 1, seed=5, T0=2000.0, T1=2000.0)
+    got = gpu_anneal(h, 2, 1, 5, T0=2000.0, T1=2000.0)
+    assert_same(got, ref, [1])
+    with pytest.raises(qpath.QpError):
+        qpath.qp_build_qubo(inputs.rect(64, 65))  # one cell more than the limit
+
+
 @pytest.mark.parametrize("kname,kernel", STRUCT_KERNELS)
 @pytest.mark.parametrize("rpc", [1, 2, 3, 8, 16])
 def test_structured_replicas_per_cta(dev, orc, rpc, kname, kernel):
