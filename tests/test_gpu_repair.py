@@ -171,6 +171,24 @@ def test_repair_large_field_greedy(dev, orc):
     assert (L1 <= L).all()
 
 
+def test_repair_at_1024_cells(dev, orc):
+    """A 32 x 32 field (1024 cells; 8.3 KB of path, edge and used-cell buffers
+    per warp): the greedy fix against the reference on sampled states, one
+    2-opt pass by its properties on all of them."""
+    f = inputs.rect(32, 32, start=527)
+    Pr = problem(orc, f)
+    C, s = Pr.C, Pr.start_cell
+    assert C == 1024
+    h = qpath.qp_build_qubo(f)
+    X = mixed_states(C, 6, seed=41, s=s)
+    P, L, S = gpu_repair(h, X, 0)
+    check_properties(P, L, S, Pr.d, C, s)
+    check_against_reference(P, L, S, X, Pr.d, C, s, 0, [0, 1, 3])
+    P1, L1, S1 = gpu_repair(h, X, 1)
+    check_properties(P1, L1, S1, Pr.d, C, s)
+    assert (L1 <= L).all()
+
+
 def test_repair_rejects_generic_qubo(dev):
     S = np.zeros((4, 4), np.int32)
     h = qpath.qp_build_from_dense(S)
