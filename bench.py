@@ -271,10 +271,21 @@ def bench_warm_start():
     ev = inputs.fields_8_16(4, seed=999999, square=16)
     rows = warmstart.evaluate(m, ev, replicas=1024, n_sweeps=2000, ref_sweeps=5000)
     s = warmstart.summarize(rows)
+    # the same comparison with every arm's states repaired into 2-opt-polished
+    # paths at each checkpoint (the reference run and the seed too)
+    rows_r = warmstart.evaluate(m, ev, replicas=1024, n_sweeps=2000, ref_sweeps=5000, repair_passes=-1)
+    sr = warmstart.summarize(rows_r)
     return {"metric": "seconds to within 1% of the best known path (mean over fields that reached it)",
             "learned_s": s["learned"]["mean_s"], "learned_reached": f'{s["learned"]["reached"]}/{s["learned"]["of"]}',
             "plain_s": s["plain"]["mean_s"], "plain_reached": f'{s["plain"]["reached"]}/{s["plain"]["of"]}',
             "plain_final_gap": s["mean_gap_plain_final"], "learned_seed_gap": s["mean_gap_seed"],
+            "with_repair": {"learned_s": sr["learned"]["mean_s"],
+                            "learned_reached": f'{sr["learned"]["reached"]}/{sr["learned"]["of"]}',
+                            "plain_s": sr["plain"]["mean_s"],
+                            "plain_reached": f'{sr["plain"]["reached"]}/{sr["plain"]["of"]}',
+                            "plain_final_gap": sr["mean_gap_plain_final"],
+                            "learned_final_gap": sr["mean_gap_learned_final"],
+                            "learned_seed_gap": sr["mean_gap_seed"]},
             "fields": "4 held-out 16x16 (seed 999999), A = 2 max d, 1024 replicas x 2000 sweeps per arm",
             "training": f"{len(data)} fields, {len(losses)} steps, loss {losses[0]:.3f} -> {losses[-1]:.3f}, "
                         f"labels+training {prep:.1f} s"}

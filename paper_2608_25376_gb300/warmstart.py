@@ -154,21 +154,45 @@ class Arm:
         v = int(self.best.min().item())
         return None if v == qpath.E_NONE else v // B
 
+    def repaired_length(self, passes=-1):
+        """Shortest path over the replicas' current states after the repair
+        (greedy fix + 2-opt, qp_repair_batch), kept as a running minimum."""
+        import torch
+        C = self.h.info["C"]
+        paths = torch.empty((self.R, C), dtype=torch.int32, device="cuda")
+        lens = torch.empty(self.R, dtype=torch.int64, device="cuda")
+        qpath.qp_repair_batch(self.h, self.R, self.a, passes, paths, lens, stream=self.stream)
+        if self.stream is not None:
+            self.stream.synchronize()
+        v = int(lens.min().item())
+        self.best_rep = min(getattr(self, "best_rep", v), v)
+        return self.best_rep
 
-def time_to_target(handle, arms, target, segments, seed_time=0.0):
+
+def time_to_target(handle, arms, target, segments, seed_time=0.0, repair_passes=None):
     """Advance every arm segment by segment (arms run concurrently, one stream
     each); -> (seconds until the best length <= target or None, final best,
-    trace [(seconds, best)])."""
+    trace [(seconds, best)]).  With repair_passes set, an arm's best also
+    counts its current states repaired into paths (the repair is on the
+    clock)."""
     import torch
     t0 = time.perf_counter() - seed_time
     trace, hit = [], None
     total = max(a.S for a in arms)
     per = max(1, total // segments)
+
+    def arm_best(a):
+        b = a.best_length()
+        if repair_passes is None:
+            return b
+        r = a.repaired_length(repair_passes)
+        return r if b is None else min(b, r)
+
     while any(a.done < a.S for a in arms):
         for a in arms:
             a.advance(per)
         torch.cuda.synchronize()
-        bests = [a.best_length() for a in arms]
+        bests = [arm_best(a) for a in arms]
         best = min([b for b in bests if b is not None], default=None)
         t = time.perf_counter() - t0
         trace.append((t, best))
@@ -178,13 +202,17 @@ def time_to_target(handle, arms, target, segments, seed_time=0.0):
 
 
 def evaluate(model, fields, replicas=1024, n_sweeps=2000, seeded_fraction=0.25, T0=1e3, T1=1.0,
-             seed_T0=None, segments=20, ref_sweeps=10000, seed=3, penalty=None, decode="walk", log=None):
+             seed_T0=None, segments=20, ref_sweeps=10000, seed=3, penalty=None, decode="walk", log=None,
+             repair_passes=None):
     """Time-to-within-1% on each field, learned arm vs plain arm.
 
     best known = min over: a long plain reference run (ref_sweeps), the plain
     arm, the learned arm (its seed included).  Learned arm: seeded_fraction of
     the replicas start from the decoded prediction at seed_T0 (default A/4),
-    the rest anneal plainly; its clock includes features, forward and decode."""
+    the rest anneal plainly; its clock includes features, forward and decode.
+    With repair_passes set, every arm (the reference run and the seed too) is
+    also judged by its states repaired into paths with that many 2-opt passes
+    (qp_repair_batch; -1 = until no move helps), the repair on the clock."""
     import torch
     rows = []
     s_main, s_side = torch.cuda.Stream(), torch.cuda.Stream()
@@ -208,17 +236,24 @@ def evaluate(model, fields, replicas=1024, n_sweeps=2000, seeded_fraction=0.25, 
             ref.advance(ref.S)
         torch.cuda.synchronize()
         ref_best = ref.best_length()
+        if repair_passes is not None:
+            r = ref.repaired_length(repair_passes)
+            ref_best = r if ref_best is None else min(ref_best, r)
         # plain arm (record the trace; the target is fixed afterwards)
         plain = Arm(h, replicas, n_sweeps, T0, T1, seed, 0, stream=s_main)
-        _, plain_best, plain_trace = time_to_target(h, [plain], -1, segments)
+        _, plain_best, plain_trace = time_to_target(h, [plain], -1, segments, repair_passes=repair_passes)
         # learned arm
         torch.cuda.synchronize()
         t = time.perf_counter()
         state, seed_len = learned_seed(model, f, h, decode=decode)
+        if repair_passes is not None:
+            _, rep_len, _ = qpath.qp_repair_path(h, state, repair_passes)
+            seed_len = min(seed_len, rep_len)
         seeded = Arm(h, Rs, n_sweeps, sT0, T1, seed, 0, init=state, stream=s_main)
         rest = Arm(h, replicas - Rs, n_sweeps, T0, T1, seed, Rs, stream=s_side)
         seed_time = time.perf_counter() - t
-        _, learned_best, learned_trace = time_to_target(h, [seeded, rest], -1, segments, seed_time=seed_time)
+        _, learned_best, learned_trace = time_to_target(h, [seeded, rest], -1, segments, seed_time=seed_time,
+                                                        repair_passes=repair_passes)
         candidates = [x for x in (ref_best, plain_best, learned_best, seed_len) if x is not None]
         best_known = min(candidates)
         target = 1.01 * best_known
