@@ -28,7 +28,9 @@
  *   Schedule.  T_s = T0*(T1/T0)^(s/(n_sweeps-1)) (T0 if n_sweeps == 1).
  *     Proposal k in sweep s is accepted iff dE <= 0, or dE < len_s and
  *     u < floor(2^32 exp(-dE/T_s)); len_s is the first dE whose threshold is 0.
- *     Tables are built on the host in double precision.
+ *     Tables are built on the host in double precision, once per device and
+ *     schedule, and cached (the least recently used dropped first beyond
+ *     4 GiB of tables; a batch keeps its schedule's tables for its life).
  *   Sweeps.  Sweep s proposes every free k once, in increasing k.
  *   Best energy.  Minimum of E over the ends of the sweeps run at which every
  *     row and column sum is 1 (no test for a QUBO without path structure);
@@ -194,7 +196,8 @@ qp_status qp_anneal_ex(qp_handle *h, int32_t replicas, const qp_schedule *sched,
  * device memory (QP_EINVAL otherwise); init_states and best_out may be NULL.
  * The schedule's threshold tables must already exist on the device: one
  * earlier qp_anneal/qp_anneal_ex call with the same n_sweeps, T0 and T1 builds
- * them (QP_EINVAL otherwise).  The first call on each device looks up the
+ * them, and they stay cached unless more than 4 GiB of other schedules' tables
+ * were built since (QP_EINVAL otherwise).  The first call on each device looks up the
  * array's device address; make that first call before any stream capture.
  * Every call shares the one array, and each kernel rewrites the part it uses
  * before reading it, so nothing carries over between calls; calls that overlap

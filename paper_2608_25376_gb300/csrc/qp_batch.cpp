@@ -23,6 +23,7 @@ struct qp_batch {
   int dev = 0;
   int count = 0, R = 0, Cmax = 0, W = 0, blocks = 0, n_units = 0;
   DevBuf fields, units, counter;
+  std::shared_ptr<const void> sched_keep;  // the schedule's tables, referenced by the captured graph
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -61,7 +62,7 @@ extern "C" qp_status qp_batch_create(qp_handle *const *hs, int32_t count, int32_
   while (W > 1 && !batch_supported(Cmax, W)) --W;
   if (!batch_supported(Cmax, W)) return fail(QP_ERANGE, "largest field (%d cells) too large for the batch kernel", Cmax);
   DeviceSchedule sched;
-  QP_TRY(device_schedule(*sc, &sched));
+  QP_TRY(device_schedule(*sc, &sched, &b->sched_keep));
   std::vector<StructArgs> fa(count);
   for (int f = 0; f < count; ++f) {
     const qp_handle *h = hs[f];

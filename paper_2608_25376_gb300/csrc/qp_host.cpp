@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <chrono>
@@ -104,27 +105,53 @@ namespace {
 struct SchedEntry {
   DevBuf thr, off, len, c;
   DeviceSchedule view;
+  size_t bytes = 0;
+  uint64_t last_use = 0;
 };
 
-std::mutex g_sched_mu;
-std::map<SchedKey, std::unique_ptr<SchedEntry>> g_sched;
-}  // namespace
+// Schedules cached per device, least recently used dropped first once the
+// tables exceed kSchedCacheBytes.  Entries are shared: a caller keeps the
+// tables it launches with alive for as long as it holds its reference (a
+// batch for its whole life), and the device memory is freed by the last
+// holder; cudaFree waits for the device, so no kernel still reading the
+// tables can see them go.
+constexpr size_t kSchedCacheBytes = size_t(4) << 30;
 
-// Device tables of a schedule (all n_sweeps sweeps), built once per device and
-// kept until the process exits.
-qp_status device_schedule(const qp_schedule &sc, DeviceSchedule *out) {
-  int dev = 0;
-  QP_CU(cudaGetDevice(&dev));
+// The cache's size limit: QPATH_SCHEDULE_CACHE_MB (MiB) when set, else 4 GiB.
+size_t sched_cache_limit() {
+  const char *v = std::getenv("QPATH_SCHEDULE_CACHE_MB");
+  if (v && *v) {
+    const long long mb = std::atoll(v);
+    if (mb > 0) return (size_t)mb << 20;
+  }
+  return kSchedCacheBytes;
+}
+std::mutex g_sched_mu;
+std::map<SchedKey, std::shared_ptr<SchedEntry>> g_sched;
+size_t g_sched_bytes = 0;
+uint64_t g_sched_clock = 0;
+
+SchedKey key_of(int dev, const qp_schedule &sc) {
   SchedKey key{dev, sc.n_sweeps, 0, 0};
   std::memcpy(&key.t0, &sc.T0, 8);
   std::memcpy(&key.t1, &sc.T1, 8);
+  return key;
+}
+}  // namespace
+
+qp_status device_schedule(const qp_schedule &sc, DeviceSchedule *out, std::shared_ptr<const void> *keep) {
+  int dev = 0;
+  QP_CU(cudaGetDevice(&dev));
+  const SchedKey key = key_of(dev, sc);
   std::lock_guard<std::mutex> lk(g_sched_mu);
   auto it = g_sched.find(key);
   if (it != g_sched.end()) {
+    it->second->last_use = ++g_sched_clock;
     *out = it->second->view;
+    if (keep) *keep = it->second;
     return QP_OK;
   }
-  auto e = std::make_unique<SchedEntry>();
+  auto e = std::make_shared<SchedEntry>();
   std::vector<int64_t> off(sc.n_sweeps);
   std::vector<int32_t> len(sc.n_sweeps);
   std::vector<float> cf(sc.n_sweeps);
@@ -180,7 +207,20 @@ qp_status device_schedule(const qp_schedule &sc, DeviceSchedule *out) {
   e->view.n_sweeps = sc.n_sweeps;
   e->view.max_len = max_len;
   e->view.total = (int64_t)all.size();
+  e->bytes = all.size() * 4 + off.size() * 8 + len.size() * 4 + cf.size() * 4;
+  e->last_use = ++g_sched_clock;
+  // make room: drop the least recently used schedules (their holders keep them alive)
+  const size_t limit = sched_cache_limit();
+  while (g_sched_bytes + e->bytes > limit && !g_sched.empty()) {
+    auto lru = g_sched.begin();
+    for (auto j = g_sched.begin(); j != g_sched.end(); ++j)
+      if (j->second->last_use < lru->second->last_use) lru = j;
+    g_sched_bytes -= lru->second->bytes;
+    g_sched.erase(lru);
+  }
   *out = e->view;
+  if (keep) *keep = e;
+  g_sched_bytes += e->bytes;
   g_sched.emplace(key, std::move(e));
   return QP_OK;
 }
@@ -445,7 +485,8 @@ extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc
   DevSet ds(h->dev);
   cudaStream_t st = static_cast<cudaStream_t>(stream_);
   DeviceSchedule sched;
-  QP_TRY(device_schedule(*sc, &sched));
+  std::shared_ptr<const void> sched_keep;  // the tables stay alive until the launch is queued
+  QP_TRY(device_schedule(*sc, &sched, &sched_keep));
   const size_t n = (size_t)h->n;
 
   // stage host buffers
@@ -621,16 +662,16 @@ bool handle_struct_view(const qp_handle *h, StructView *out) {
   return true;
 }
 
-bool schedule_lookup(const qp_schedule &sc, DeviceSchedule *out) {
+bool schedule_lookup(const qp_schedule &sc, DeviceSchedule *out, std::shared_ptr<const void> *keep) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
-  SchedKey key{dev, sc.n_sweeps, 0, 0};
-  std::memcpy(&key.t0, &sc.T0, 8);
-  std::memcpy(&key.t1, &sc.T1, 8);
+  const SchedKey key = key_of(dev, sc);
   std::lock_guard<std::mutex> lk(g_sched_mu);
   auto it = g_sched.find(key);
   if (it == g_sched.end()) return false;
+  it->second->last_use = ++g_sched_clock;
   *out = it->second->view;
+  if (keep) *keep = it->second;
   return true;
 }
 

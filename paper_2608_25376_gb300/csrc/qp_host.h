@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -94,8 +95,9 @@ double temperature(const qp_schedule &sc, int s);
 void build_thresholds(double T, std::vector<uint32_t> &out);
 qp_status check_schedule(const qp_schedule *sc);
 // Device tables of a schedule (all n_sweeps sweeps), built once per device and
-// kept until the process exits.
-qp_status device_schedule(const qp_schedule &sc, DeviceSchedule *out);
+// cached (least recently used dropped first beyond 4 GiB of tables).  *keep
+// (may be NULL) holds the tables alive while the caller needs them.
+qp_status device_schedule(const qp_schedule &sc, DeviceSchedule *out, std::shared_ptr<const void> *keep);
 
 }  // namespace host
 }  // namespace qp

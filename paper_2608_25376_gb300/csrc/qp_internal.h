@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <string>
 
 #include "qpath.h"
@@ -138,7 +139,8 @@ struct StructView {
   bool d_i16;
 };
 bool handle_struct_view(const qp_handle *h, StructView *out);  // false for a generic QUBO
-bool schedule_lookup(const qp_schedule &sc, DeviceSchedule *out);  // false if never built here
+// false if not cached on this device; *keep (may be NULL) holds the tables alive
+bool schedule_lookup(const qp_schedule &sc, DeviceSchedule *out, std::shared_ptr<const void> *keep);
 qp_status set_error(qp_status s, const char *msg);
 bool device_pointer(const void *p);
 

@@ -70,7 +70,8 @@ extern "C" qp_status qp_anneal_noalloc(qp_handle *h, int32_t R, const qp_schedul
       (init && !device_pointer(init)))
     return set_error(QP_EINVAL, "qp_anneal_noalloc: every buffer must be device memory");
   DeviceSchedule sched;
-  if (!schedule_lookup(*sc, &sched))
+  std::shared_ptr<const void> sched_keep;  // the tables stay alive until the launch is queued
+  if (!schedule_lookup(*sc, &sched, &sched_keep))
     return set_error(QP_EINVAL,
                      "qp_anneal_noalloc: the schedule's threshold tables do not exist on this device yet; "
                      "make one qp_anneal/qp_anneal_ex call with the same n_sweeps, T0, T1 first");

@@ -107,7 +107,7 @@ extern "C" qp_status qp_anneal_timed(qp_handle *h, int32_t R, const qp_schedule 
   int64_t *E = h->t_E.as<int64_t>(), *Ld = h->t_len.as<int64_t>();
   int32_t *Pd = h->t_paths.as<int32_t>(), *Sd = h->t_stat.as<int32_t>();
   DeviceSchedule dsched;
-  QP_TRY(device_schedule(full, &dsched));
+  QP_TRY(device_schedule(full, &dsched, nullptr));  // build the tables before the rounds
 
   std::vector<int64_t> len(R), en(R);
   std::vector<int32_t> stat(R);

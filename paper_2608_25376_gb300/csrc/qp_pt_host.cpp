@@ -88,7 +88,8 @@ extern "C" qp_status qp_anneal_pt(qp_handle *h, int32_t G, const qp_pt_schedule 
   DevSet ds(h->dev);
   cudaStream_t st = static_cast<cudaStream_t>(stream_);
   DeviceSchedule lt;
-  QP_TRY(device_schedule(ladder, &lt));
+  std::shared_ptr<const void> ladder_keep;  // the ladder's tables stay alive through the rounds
+  QP_TRY(device_schedule(ladder, &lt, &ladder_keep));
   const uint32_t *xthr = nullptr;
   const int64_t *xoff = nullptr;
   const int32_t *xlen = nullptr;
