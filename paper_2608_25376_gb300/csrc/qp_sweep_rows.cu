@@ -14,17 +14,20 @@
 //   dE = base - 2A + 2A r          (x = 0)
 //   dE = 6A - base - 2A r          (x = 1),     base = B (F_{t-1} + F_{t+1})(i) + 2A c_i.
 // A row chunk (128 proposals) is first tested as a whole: a proposal matters
-// only if dE <= 0 or 1 <= dE < len_s (one add and one unsigned compare), and
-// at low temperature most rows have none, so they cost a few instructions per
-// proposal.  Otherwise the warp evaluates the chunk against the current state,
-// a ballot finds the first accepted proposal, the flip is applied and
-// evaluation resumes after it: exactly the sequential order.  The spins are a bitset per row (Cw = ceil(C/32) words) in
-// shared memory; the distance matrix is staged in shared memory (widened to
-// int32 when that fits) or read from L2.
+// only if dE < len_s (accepted outright when dE <= 0, decided by a draw when
+// 1 <= dE < len_s), one compare each, and at low temperature most rows have
+// none, so they cost a few instructions per proposal.  Otherwise the warp
+// evaluates the chunk against the current state, a ballot finds the first
+// accepted proposal, the flip is applied and evaluation resumes after it:
+// exactly the sequential order.  The spins are a bitset per row
+// (Cw = ceil(C/32) words) in shared memory; the distance matrix is staged in
+// shared memory (widened to int32 when that fits) or read from L2.
 //
 // The draw of x_{t,i} is word k&3 of Philox4x32-10(counter = (k>>2, sweep,
 // replica, tag)), k = t*C + i; a lane's four proposals span one or two counter
 // blocks, each computed only when one of its proposals has 1 <= dE < len_s.
+// Most draws are rejected by two integer compares (u >= thr[dq] with
+// dq ~ 8 T ln 2 and dE >= dq) before the float estimate of exp(-dE/T).
 #include <climits>
 
 #include "qp_device.cuh"
