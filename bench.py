@@ -679,8 +679,23 @@ def run_profile_case(args):
             loss = qpath.qp_ws_train_step(m, X, Y, T, 1e-3)
             torch.cuda.synchronize()
             times.append((time.perf_counter() - t0) * 1e3)
+        # forward only, fused (one launch) and layered (four GEMM launches):
+        # host time of the call, logits written to device memory
+        Z = torch.empty((M, qpath.WS_STEPS), dtype=torch.float32, device="cuda")
+        fwd = {}
+        for name, mode in (("fused", qpath.QP_WS_FORWARD_FUSED), ("layered", qpath.QP_WS_FORWARD_LAYERED)):
+            qpath.qp_ws_set_forward_mode(m, mode)
+            ts = []
+            for _ in range(4):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                qpath.qp_ws_forward(m, X, Z)
+                torch.cuda.synchronize()
+                ts.append((time.perf_counter() - t0) * 1e3)
+            fwd[name] = ts
+        qpath.qp_ws_set_forward_mode(m, qpath.QP_WS_FORWARD_FUSED)
         print(json.dumps({"profile_case": "mlp", "cells": M, "ms": times, "loss": loss,
-                          "flops_per_layer_fwd": 2 * M * 256 * 256}))
+                          "forward_ms": fwd, "flops_per_layer_fwd": 2 * M * 256 * 256}))
         return 0
     w = inputs.WORKLOADS[args.workload]
     f = w["field"]()

@@ -386,6 +386,15 @@ qp_status qp_ws_features(const qp_field *field, float *feats_out, int32_t *n_cel
  * device).  QP_ETIMEOUT if a tensor-core wait gave up. */
 qp_status qp_ws_forward(qp_ws *ws, const float *feats, int32_t M, float *logits_out, void *cuda_stream);
 
+/* How the forward pass (of qp_ws_forward, _grads, _train_step, _infer) runs:
+ * QP_WS_FORWARD_FUSED (the default) is one launch for all four layers, each
+ * 128-cell tile's activations kept in shared memory between layers;
+ * QP_WS_FORWARD_LAYERED is one tensor-core GEMM launch per layer, the
+ * activations through global memory.  Both issue the same MMAs in the same
+ * order, so their logits are bit-identical.  QP_EINVAL for another mode. */
+enum { QP_WS_FORWARD_FUSED = 0, QP_WS_FORWARD_LAYERED = 1 };
+qp_status qp_ws_set_forward_mode(qp_ws *ws, int32_t mode);
+
 /* Gradients of the mean cross-entropy over M cells without updating: labels
  * (M int32: the cell's step, -1 = ignore), steps (M int32: the cell's field
  * size C, logits t >= C are masked).  grads_out (param_count floats, host, may

@@ -316,6 +316,246 @@ __global__ void __launch_bounds__(128)
   if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
+// ----------------------------------------------------------------------------- fused forward
+// The whole network for one 128-row tile in one CTA.  The tile's activations
+// stay in shared memory (K-major, 256 columns: 64 KB, four 128 x 64 blocks in
+// the 128-byte swizzle layout a tile copy would write) as the A operand of
+// every layer.  The weights (N = 256 rows, K-major) come in
+// 64-column chunks by tensor-map tile copies (128-byte swizzle) through four
+// 32 KB stages: 13 chunks in all (one for the 16-feature layer, four for each
+// other layer), chunk j in stage j % 4, its copy issued as soon as the MMAs
+// of chunk j - 4 are complete, so the next layer's weights land while the
+// current layer's epilogue runs.  One thread issues each chunk's MMAs as soon
+// as its weights have landed and only then waits for the chunk before it, so
+// the tensor pipe is never drained between chunks.  The accumulator (128 x
+// 256 fp32, 256 TMEM columns) is read back by the epilogue (bias from shared
+// memory, ReLU, bf16), which writes the next layer's input over the
+// activations once the layer's MMAs are complete; when the hidden
+// activations are asked for (training keeps them for the backward pass) the
+// CTA copies them to global memory in full sectors while the next layer's
+// MMAs run.  The last layer's fp32 logits are staged per warp in shared
+// memory and written in 512-byte rows.  Eight warps: warp w reads TMEM lanes
+// 32 (w mod 4) .. +31 (its rows) and accumulator columns 128 (w / 4) .. +127.
+// Every wait is bounded; TMEM is always freed.
+constexpr int kFwdLayers = 4;
+constexpr int kFwdChunks = 13;
+constexpr int kFwdStages = 4;
+constexpr size_t kActBytes = (size_t)kTileM * 256 * 2;
+constexpr size_t kWStage = 256 * kChunkK * 2;  // 32 KB
+constexpr size_t kBiasBytes = (size_t)kFwdLayers * 256 * 4;
+constexpr int kFwdThreads = 256;
+constexpr int kZRow = 512 + 16;  // staged half logit row: 128 fp32 + 16 bytes against bank conflicts
+constexpr size_t kFwdSmem = 1024 + kActBytes + kFwdStages * kWStage + kBiasBytes;
+static_assert((kFwdThreads / 32) * 32 * kZRow <= kActBytes + kFwdStages * kWStage,
+              "logit staging exceeds the free buffers");
+static_assert(kFwdSmem <= 227 * 1024, "fused forward exceeds the shared-memory budget");
+
+struct FwdTmaps {
+  CUtensorMap w[kFwdLayers];
+};
+
+// Byte offset of the 16-byte segment `seg` (8 columns) of row r in the
+// activation tile: block seg / 8 (64 columns, 16 KB), row r at 128 r, its
+// 16-byte pieces permuted by the 128-byte swizzle (piece index XOR r mod 8).
+__device__ __forceinline__ uint32_t act_offset(int r, int seg) {
+  return (uint32_t)((seg >> 3) * (kTileM * 128) + r * 128 + (((seg & 7) ^ (r & 7)) << 4));
+}
+
+// 64 consecutive fp32 columns of this thread's TMEM lane; the wait is in the
+// same statement, so no use of the registers can be scheduled before it.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(kFwdThreads)
+    k_mlp_forward(const __grid_constant__ FwdTmaps tm, const __grid_constant__ FwdArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t full[kFwdStages], done[kFwdStages];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail_flag;
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *act = smem;
+  uint8_t *wst = smem + kActBytes;
+  float *bias_s = reinterpret_cast<float *>(wst + kFwdStages * kWStage);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quad = warp & 3, half = warp >> 2;  // TMEM lane quarter, accumulator column half
+  const int trow = quad * 32 + lane;            // the tile row this thread reads back
+  const int m0 = blockIdx.x * kTileM;
+
+  if (warp == 0) tmem_alloc(smem_u32(&tmem_slot), kTmemCols);
+  if (tid == 0) {
+    for (int s = 0; s < kFwdStages; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&done[s]), 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int l = 0; l < kFwdLayers; ++l)
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm.w[l])) : "memory");
+    fail_flag = 0;
+  }
+  // the biases, and layer 1's input: the tile's 16 features (bf16) into core-matrix columns 0..15
+  for (int i = tid; i < kFwdLayers * 256; i += kFwdThreads) bias_s[i] = g.bias[i >> 8][i & 255];
+  if (tid < kTileM) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(g.x0 + (size_t)(m0 + tid) * 16);
+    const uint4 a = src[0], b = src[1];
+    *reinterpret_cast<uint4 *>(act + act_offset(tid, 0)) = a;
+    *reinterpret_cast<uint4 *>(act + act_offset(tid, 1)) = b;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = idesc_bf16(kTileM, 256);
+  const uint32_t act_a = smem_u32(act);
+  const uint32_t wst_a = smem_u32(wst);
+  // chunk j: layer 0 for j = 0, else layer 1 + (j - 1) / 4, K columns 64 ((j - 1) % 4) ...
+  auto layer_of = [](int j) { return j == 0 ? 0 : 1 + (j - 1) / 4; };
+  auto chunk_in_layer = [](int j) { return j == 0 ? 0 : (j - 1) % 4; };
+  uint32_t done_seen = 0;  // bit j: the MMAs of chunk j have been waited for
+  uint32_t full_seen = 0;  // bit j: the weights of chunk j have been waited for
+  int issued = 0;          // chunks whose tile copy has been issued (in order)
+  int committed = 0;       // chunks whose MMAs have been committed (in order)
+  auto issue = [&](int j) {
+    const int s = j % kFwdStages;
+    mbar_expect_tx(smem_u32(&full[s]), (uint32_t)kWStage);
+    tma_load_2d(wst_a + s * (uint32_t)kWStage, &tm.w[layer_of(j)], chunk_in_layer(j) * kChunkK, 0,
+                smem_u32(&full[s]));
+    ++issued;
+  };
+  // chunk j is the (j / 4)-th use of stage j % 4, hence phase parity (j / 4) & 1;
+  // chunk j + 4 is issued only after the MMAs of chunk j completed, so no wait
+  // ever looks at a phase two completions old
+  auto wait_done = [&](int j) -> bool {
+    if ((done_seen >> j) & 1u) return true;
+    if (!mbar_wait(smem_u32(&done[j % kFwdStages]), (j / kFwdStages) & 1)) return false;
+    done_seen |= 1u << j;
+    return true;
+  };
+  auto wait_full = [&](int j) -> bool {
+    if ((full_seen >> j) & 1u) return true;
+    if (!mbar_wait(smem_u32(&full[j % kFwdStages]), (j / kFwdStages) & 1)) return false;
+    full_seen |= 1u << j;
+    return true;
+  };
+  // after chunk j's MMAs are complete its stage takes chunk j + 4
+  auto refill = [&](int j) {
+    if (j + kFwdStages < kFwdChunks && issued == j + kFwdStages) issue(j + kFwdStages);
+  };
+  if (tid == 0)
+    for (int j = 0; j < kFwdStages; ++j) issue(j);
+
+  int j0 = 0;  // first chunk of the current layer
+  for (int l = 0; l < kFwdLayers; ++l) {
+    const int nch = l == 0 ? 1 : 4;  // weight chunks of the layer
+    bool ok = true;
+    if (tid == 0 && !fail_flag) {
+      for (int c = 0; c < nch && ok; ++c) {
+        const int j = j0 + c, s = j % kFwdStages;
+        ok = wait_full(j);
+        if (!ok) break;
+        tc_fence_after();
+        const int ksteps = l == 0 ? 1 : 4;
+        for (int kk = 0; kk < ksteps; ++kk) {
+          const uint64_t ad = smem_desc_sw128(act_a + (uint32_t)c * (kTileM * 128) + kk * 32);
+          const uint64_t bd = smem_desc_sw128(wst_a + s * (uint32_t)kWStage + kk * 32);
+          mma_bf16(tmem, ad, bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+        }
+        mma_commit(smem_u32(&done[s]));
+        ++committed;
+        if (c > 0) {  // the chunk before is complete once this one is queued behind it
+          ok = wait_done(j - 1);
+          if (ok) refill(j - 1);
+        }
+      }
+    }
+    // the previous layer's activations to global memory (16 rows x 64 bytes
+    // per warp instruction) while this layer's MMAs read them
+    if (l > 0 && g.h[l - 1]) {
+      __nv_bfloat16 *hg = g.h[l - 1];
+      for (int it = warp; it < 128; it += kFwdThreads / 32) {  // 16 row groups x 8 quads of segments
+        const int r = (it >> 3) * 8 + (lane & 7), seg = (it & 7) * 4 + (lane >> 3);
+        const uint4 u = *reinterpret_cast<const uint4 *>(act + act_offset(r, seg));
+        *reinterpret_cast<uint4 *>(hg + (size_t)(m0 + r) * 256 + seg * 8) = u;
+      }
+    }
+    if (tid == 0 && !fail_flag) {
+      if (ok) ok = wait_done(j0 + nch - 1);  // the layer's accumulator is complete
+      if (ok) refill(j0 + nch - 1);
+      if (!ok) fail_flag = 1;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (fail_flag) break;
+    __syncwarp();  // the warp-wide tcgen05.ld below needs the whole warp converged
+    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+    const float4 *bl = reinterpret_cast<const float4 *>(bias_s + l * 256);
+    if (l < kFwdLayers - 1) {
+      // accumulator row trow -> + bias, ReLU, bf16 -> the next layer's input
+      for (int q = half * 2; q < half * 2 + 2; ++q) {
+        uint32_t r[64];
+        tmem_ld64(lane_base + q * 64, r);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {  // 8 columns = one 16-byte segment
+          const float4 b0 = bl[q * 16 + 2 * p], b1 = bl[q * 16 + 2 * p + 1];
+          const float x[8] = {__uint_as_float(r[8 * p]) + b0.x,     __uint_as_float(r[8 * p + 1]) + b0.y,
+                              __uint_as_float(r[8 * p + 2]) + b0.z, __uint_as_float(r[8 * p + 3]) + b0.w,
+                              __uint_as_float(r[8 * p + 4]) + b1.x, __uint_as_float(r[8 * p + 5]) + b1.y,
+                              __uint_as_float(r[8 * p + 6]) + b1.z, __uint_as_float(r[8 * p + 7]) + b1.w};
+          uint32_t w[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(fmaxf(x[2 * i], 0.0f), fmaxf(x[2 * i + 1], 0.0f));
+            w[i] = *reinterpret_cast<const uint32_t *>(&b2);
+          }
+          *reinterpret_cast<uint4 *>(act + act_offset(trow, q * 8 + p)) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      }
+      // the new activations are the next layer's A operand (read by the async proxy)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+    } else {
+      // logits: every MMA is complete and every copy consumed, so the
+      // activation and weight buffers are free; each warp stages its 32 half rows
+      uint8_t *zw = smem + (size_t)warp * 32 * kZRow;
+      for (int q = half * 2; q < half * 2 + 2; ++q) {
+        uint32_t r[64];
+        tmem_ld64(lane_base + q * 64, r);
+#pragma unroll
+        for (int p = 0; p < 16; ++p) {
+          const float4 b = bl[q * 16 + p];
+          *reinterpret_cast<float4 *>(zw + (size_t)lane * kZRow + ((q - half * 2) * 16 + p) * 16) =
+              make_float4(__uint_as_float(r[4 * p]) + b.x, __uint_as_float(r[4 * p + 1]) + b.y,
+                          __uint_as_float(r[4 * p + 2]) + b.z, __uint_as_float(r[4 * p + 3]) + b.w);
+        }
+      }
+      __syncwarp();
+      for (int rr = 0; rr < 32; ++rr) {
+        float *zg = g.z + (size_t)(m0 + quad * 32 + rr) * 256 + half * 128;
+        *reinterpret_cast<float4 *>(zg + lane * 4) = *reinterpret_cast<const float4 *>(zw + (size_t)rr * kZRow + lane * 16);
+      }
+    }
+    j0 += nch;
+  }
+  if (tid == 0) {
+    // let every copy and MMA still in flight land (bounded) before the CTA exits
+    for (int j = 0; j < issued; ++j) wait_full(j);
+    for (int j = 0; j < committed; ++j) wait_done(j);
+    if (fail_flag && g.err) atomicExch(g.err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
 // Softmax cross-entropy over the valid steps t < steps[m] of each cell row;
 // rows with label < 0 are padding.  dZ = (softmax - onehot) * inv_rows (bf16),
 // loss_sum += -log p[label].  One warp per row, 8 columns per lane.
@@ -470,6 +710,23 @@ cudaError_t gemm(const GemmArgs &g, int splits, cudaStream_t st) {
   const int zs = (g.K + kps - 1) / kps;
   dim3 grid((g.M + kTileM - 1) / kTileM, 1, zs);
   k_gemm_tc<<<grid, 128, kGemmSmem, st>>>(ta, tb, a);
+  return cudaGetLastError();
+}
+
+cudaError_t forward(const FwdArgs &g, const __nv_bfloat16 *const w[4], cudaStream_t st) {
+  if (g.Mp <= 0 || (g.Mp % kTileM) || !g.x0 || !g.z) return cudaErrorInvalidValue;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  alignas(64) FwdTmaps tm;
+  for (int l = 0; l < kFwdLayers; ++l) {
+    const int K = l == 0 ? 16 : 256;
+    if (!g.bias[l] || !tile_map(&tm.w[l], w[l], 256, K, K, 256)) return cudaErrorInvalidValue;
+  }
+  k_mlp_forward<<<g.Mp / kTileM, kFwdThreads, kFwdSmem, st>>>(tm, g);
   return cudaGetLastError();
 }
 

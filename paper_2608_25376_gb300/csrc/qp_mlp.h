@@ -35,6 +35,20 @@ struct GemmArgs {
 };
 
 cudaError_t gemm(const GemmArgs &g, int splits, cudaStream_t st);
+
+// The network's whole forward pass in one launch, one CTA per 128-row tile:
+// x0 bf16 [Mp x 16] (Mp a multiple of 128), weights w[l] bf16 [256 x K_l]
+// row-major (K_0 = 16, else 256), bias[l] fp32 [256], hidden activations
+// h[l] bf16 [Mp x 256] (null: not written), logits z fp32 [Mp x 256].
+struct FwdArgs {
+  const __nv_bfloat16 *x0;
+  const float *bias[4];
+  __nv_bfloat16 *h[3];
+  float *z;
+  int Mp;
+  int *err;  // set to 1 if a bounded wait gave up
+};
+cudaError_t forward(const FwdArgs &g, const __nv_bfloat16 *const w[4], cudaStream_t st);
 cudaError_t softmax_ce(const float *Z, int ldz, const int32_t *label, const int32_t *steps, int M, float inv_rows,
                        __nv_bfloat16 *dZ, int ldd, float *loss_sum, cudaStream_t st);
 cudaError_t colsum(const __nv_bfloat16 *Y, int ld, int M, int N, float *out, cudaStream_t st);

@@ -82,6 +82,7 @@ struct qp_ws {
   Buf gw[kLayers], gb[kLayers];        // fp32 gradients
   Buf wb[kLayers], wt[kLayers];        // bf16 weight and its transpose
   int cap = 0;                         // rows the activation buffers hold
+  int fwd_mode = QP_WS_FORWARD_FUSED;
   Buf x0, h[3], z, dz, dh[3], t1, t2, lab, stp, loss, err;
 };
 
@@ -157,7 +158,24 @@ mlp::GemmArgs gargs(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int
   return g;
 }
 
-qp_status forward(qp_ws *m, int Mp, cudaStream_t st) {
+// Logits into m->z; the hidden activations into m->h[] when keep_hidden (the
+// backward pass reads them) or when the layers run as separate launches.
+qp_status forward(qp_ws *m, int Mp, bool keep_hidden, cudaStream_t st) {
+  if (m->fwd_mode == QP_WS_FORWARD_FUSED) {
+    mlp::FwdArgs g{};
+    g.x0 = m->x0.as<__nv_bfloat16>();
+    const __nv_bfloat16 *w[kLayers];
+    for (int l = 0; l < kLayers; ++l) {
+      g.bias[l] = m->b[l].as<float>();
+      w[l] = m->wb[l].as<__nv_bfloat16>();
+    }
+    for (int l = 0; l < 3; ++l) g.h[l] = keep_hidden ? m->h[l].as<__nv_bfloat16>() : nullptr;
+    g.z = m->z.as<float>();
+    g.Mp = Mp;
+    g.err = m->err.as<int>();
+    WS_CU(mlp::forward(g, w, st));
+    return QP_OK;
+  }
   const __nv_bfloat16 *in = m->x0.as<__nv_bfloat16>();
   int ldin = kIn;
   for (int l = 0; l < kLayers; ++l) {
@@ -330,9 +348,16 @@ extern "C" qp_status qp_ws_forward(qp_ws *m, const float *feats, int32_t M, floa
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int Mp = (M + 127) / 128 * 128;
   if (qp_status s = upload_inputs(m, feats, M, Mp, nullptr, nullptr, st); s != QP_OK) return s;
-  if (qp_status s = forward(m, Mp, st); s != QP_OK) return s;
+  if (qp_status s = forward(m, Mp, false, st); s != QP_OK) return s;
   WS_CU(cudaMemcpyAsync(logits_out, m->z.p, (size_t)M * kOut * 4, cudaMemcpyDefault, st));
   return check_err(m, st);
+}
+
+extern "C" qp_status qp_ws_set_forward_mode(qp_ws *m, int32_t mode) {
+  if (!m || (mode != QP_WS_FORWARD_FUSED && mode != QP_WS_FORWARD_LAYERED))
+    return set_error(QP_EINVAL, "bad argument");
+  m->fwd_mode = mode;
+  return QP_OK;
 }
 
 extern "C" qp_status qp_ws_grads(qp_ws *m, const float *feats, const int32_t *labels, const int32_t *steps,
@@ -342,7 +367,7 @@ extern "C" qp_status qp_ws_grads(qp_ws *m, const float *feats, const int32_t *la
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int Mp = (M + 127) / 128 * 128;
   if (qp_status s = upload_inputs(m, feats, M, Mp, labels, steps, st); s != QP_OK) return s;
-  if (qp_status s = forward(m, Mp, st); s != QP_OK) return s;
+  if (qp_status s = forward(m, Mp, true, st); s != QP_OK) return s;
   if (qp_status s = backward(m, M, Mp, st); s != QP_OK) return s;
   if (qp_status s = check_err(m, st); s != QP_OK) return s;
   if (grads_out) {

@@ -30,7 +30,7 @@ SYMBOLS = ["qp_build_qubo", "qp_build_from_dense", "qp_qubo_info", "qp_export_de
            "qp_thresholds", "qp_anneal", "qp_anneal_ex", "qp_anneal_noalloc", "qp_batch_create",
            "qp_batch_run", "qp_batch_info", "qp_batch_destroy", "qp_anneal_batch", "qp_decode_path",
            "qp_decode_batch", "qp_repair_batch", "qp_repair_path", "qp_anneal_timed", "qp_anneal_pt", "qp_ws_create", "qp_ws_destroy", "qp_ws_param_count", "qp_ws_get_params",
-           "qp_ws_set_params", "qp_ws_features", "qp_ws_forward", "qp_ws_grads", "qp_ws_train_step",
+           "qp_ws_set_params", "qp_ws_features", "qp_ws_forward", "qp_ws_set_forward_mode", "qp_ws_grads", "qp_ws_train_step",
            "qp_ws_decode", "qp_ws_decode_walk", "qp_ws_infer", "qp_selftest_wait", "qp_destroy", "qp_last_error"]
 
 
@@ -108,6 +108,7 @@ def lib():
                 "qp_ws_set_params": [vp, vp],
                 "qp_ws_features": [P(qp_field), vp, P(i32)],
                 "qp_ws_forward": [vp, vp, i32, vp, vp],
+                "qp_ws_set_forward_mode": [vp, i32],
                 "qp_ws_grads": [vp, vp, vp, vp, i32, vp, vp, vp],
                 "qp_ws_train_step": [vp, vp, vp, vp, i32, ct.c_float, vp, vp],
                 "qp_ws_decode": [vp, i32, i32, i32, vp, vp],
@@ -401,6 +402,7 @@ def qp_destroy(h: Handle):
 
 # --------------------------------------------------------------------------- learned warm start
 WS_FEATURES, WS_STEPS = 16, 256
+QP_WS_FORWARD_FUSED, QP_WS_FORWARD_LAYERED = 0, 1
 
 
 class WarmStartModel:
@@ -455,6 +457,10 @@ def qp_ws_forward(m: WarmStartModel, feats, logits_out=None, stream=None):
     out = np.zeros((M, WS_STEPS), np.float32) if logits_out is None else logits_out
     _check(lib().qp_ws_forward(m.ptr, _ptr(x), M, _ptr(out), _stream(stream)))
     return out
+
+
+def qp_ws_set_forward_mode(m: WarmStartModel, mode: int):
+    _check(lib().qp_ws_set_forward_mode(m.ptr, int(mode)))
 
 
 def qp_ws_grads(m: WarmStartModel, feats, labels, steps, stream=None):

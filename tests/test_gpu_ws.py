@@ -107,3 +107,28 @@ def test_infer_equals_the_three_steps(dev):
         assert (st == ref[0]).all() and (path == ref[1]).all()
         assert path[0] == start and sorted(path.tolist()) == list(range(C))
         assert qpath.qp_decode_path(h, st) is not None
+
+
+def test_fused_forward_equals_layered(dev):
+    """The one-launch forward (activations kept in shared memory) and the
+    per-layer GEMM launches issue the same MMAs in the same order: the logits
+    are bit-identical, on ragged sizes and after training has moved the
+    weights away from their initial scale.  The gradients, computed from the
+    hidden activations either mode stores, agree up to the order of the
+    backward pass's fp32 atomic sums."""
+    m = qpath.WarmStartModel(seed=9)
+    X, Y, T = field_batch(140, seed=5)
+    for _ in range(3):
+        qpath.qp_ws_train_step(m, X[:4096], Y[:4096], T[:4096], 1e-3)
+    for M in (1, 127, 300, 8960):
+        out = {}
+        for mode in (qpath.QP_WS_FORWARD_FUSED, qpath.QP_WS_FORWARD_LAYERED):
+            qpath.qp_ws_set_forward_mode(m, mode)
+            out[mode] = (qpath.qp_ws_forward(m, X[:M]), qpath.qp_ws_grads(m, X[:M], Y[:M], T[:M]))
+        (za, (la, ga)), (zb, (lb, gb)) = out[qpath.QP_WS_FORWARD_FUSED], out[qpath.QP_WS_FORWARD_LAYERED]
+        assert np.array_equal(za, zb), (M, np.abs(za - zb).max())
+        assert abs(la - lb) <= 1e-6 * abs(lb), (M, la, lb)
+        assert np.linalg.norm(ga - gb) <= 1e-5 * np.linalg.norm(gb), M
+    qpath.qp_ws_set_forward_mode(m, qpath.QP_WS_FORWARD_FUSED)
+    with pytest.raises(qpath.QpError):
+        qpath.qp_ws_set_forward_mode(m, 2)
