@@ -13,9 +13,10 @@
 // commits them to the stage's "done" mbarrier, which frees the stage for the
 // chunk after next; the load of chunk c+1 overlaps the MMAs of chunk c.
 // Every wait is bounded.  The epilogue reads the accumulator back with
-// tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = rows of the tile) and
-// applies bias/ReLU/masking.  Split-K partial tiles are added into an fp32
-// output with atomics.
+// tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = rows of the tile), applies
+// bias/ReLU/masking and stages the rows in the freed stages, so that the
+// stores (and the ReLU reference loads) cover whole sectors.  Split-K partial
+// tiles are added into an fp32 output with atomics.
 #include <cuda.h>  // CUtensorMap and the tile-encoder types; the encoder comes from the runtime
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -40,6 +41,10 @@ constexpr int kStages = 2;
 constexpr size_t kGemmSmem = 100 * 1024;
 static_assert(kStages * (kSmemA + kSmemB) + 1024 <= kGemmSmem, "GEMM stages exceed the shared-memory budget");
 constexpr long long kWaitCycles = 1000000000LL;  // ~0.5 s at 2 GHz, then give up
+// Epilogue staging: per warp 32 rows of 64 fp32 plus 16 bytes against bank conflicts.
+constexpr int kEpiRowFloats = 64 + 4;
+constexpr int kEpiRowBytes = kEpiRowFloats * 4;
+static_assert(4 * 32 * kEpiRowBytes <= kStages * (kSmemA + kSmemB), "epilogue staging exceeds the stages");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -135,22 +140,6 @@ __device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
 
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-// 32 consecutive fp32 columns of this thread's TMEM lane (one load, one wait).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // 16 consecutive fp32 columns of this thread's TMEM lane.
@@ -259,55 +248,75 @@ __global__ void __launch_bounds__(128)
   __syncthreads();
   tc_fence_after();
   if (!fail_flag && issued > 0) {
-    const int row = m0 + warp * 32 + lane;
+    // The stages are free now (every copy landed, every MMA complete): each
+    // warp stages its 32 accumulator rows, 64 columns at a time, in shared
+    // memory, then writes them out two rows per instruction so that every
+    // global access covers whole sectors.
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < N; c0 += 32) {  // N is a multiple of 16: the last block may be half used
-      float v[32];
-      const int nc = min(32, N - c0);
-      if (nc == 32) {
-        tmem_ld32(lane_base + c0, v);
-      } else {
-        float w[16];
-        tmem_ld16(lane_base + c0, w);
+    float *stg = reinterpret_cast<float *>(smem + (size_t)warp * 32 * kEpiRowBytes);
+    const int row0 = m0 + warp * 32;
+    const bool bias = g.bias && (g.mode == kEpiBiasRelu || g.mode == kEpiBiasF32);
+    for (int c0 = 0; c0 < N; c0 += 64) {
+      const int nb = min(64, N - c0);  // a multiple of 16
+      for (int cc = 0; cc < nb; cc += 16) {
+        float v[16];
+        tmem_ld16(lane_base + c0 + cc, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = w[i];
-      }
-      if (row >= g.M) continue;
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        if (q * 16 >= nc) break;
-        const int cc = c0 + q * 16;
-        float *vv = v + q * 16;
-        if (g.mode == kEpiBiasRelu || g.mode == kEpiBiasF32) {
-#pragma unroll
-          for (int i = 0; i < 16; ++i) vv[i] += g.bias ? g.bias[cc + i] : 0.0f;
+        for (int i = 0; i < 16; ++i) {
+          float x = v[i] + (bias ? g.bias[c0 + cc + i] : 0.0f);
+          if (g.mode == kEpiBiasRelu) x = fmaxf(x, 0.0f);
+          v[i] = x;
         }
-        if (g.mode == kEpiBiasRelu) {
-          __nv_bfloat16 *o = g.out_bf16 + (size_t)row * g.ldo + cc;
 #pragma unroll
-          for (int i = 0; i < 16; i += 2)
-            *reinterpret_cast<__nv_bfloat162 *>(o + i) =
-                __floats2bfloat162_rn(fmaxf(vv[i], 0.0f), fmaxf(vv[i + 1], 0.0f));
-        } else if (g.mode == kEpiBiasF32) {
-          float *o = g.out_f32 + (size_t)row * g.ldo + cc;
+        for (int i = 0; i < 16; i += 4)
+          *reinterpret_cast<float4 *>(stg + lane * kEpiRowFloats + cc + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+      }
+      __syncwarp();
+      const int cl = 4 * (lane & 15);  // this lane's 4 columns of the block
+      // the ReLU reference of the lane's 16 (row, 4-column) pieces, all loads in flight at once
+      uint2 rref[16];
+      if (g.mode == kEpiReluMask) {
 #pragma unroll
-          for (int i = 0; i < 16; i += 4)
-            *reinterpret_cast<float4 *>(o + i) = make_float4(vv[i], vv[i + 1], vv[i + 2], vv[i + 3]);
+        for (int q = 0; q < 16; ++q) {
+          const int row = row0 + 2 * q + (lane >> 4);
+          rref[q] = (cl < nb && row < g.M)
+                        ? *reinterpret_cast<const uint2 *>(g.relu_ref + (size_t)row * g.ldr + c0 + cl)
+                        : make_uint2(0u, 0u);
+        }
+      }
+#pragma unroll
+      for (int rr = 0; rr < 32; rr += 2) {
+        const int r = rr + (lane >> 4), row = row0 + r;
+        if (cl >= nb || row >= g.M) continue;
+        const float4 x = *reinterpret_cast<const float4 *>(stg + r * kEpiRowFloats + cl);
+        const size_t col = (size_t)(c0 + cl);
+        if (g.mode == kEpiBiasF32) {
+          *reinterpret_cast<float4 *>(g.out_f32 + (size_t)row * g.ldo + col) = x;
         } else if (g.mode == kEpiAtomicF32) {
-          float *o = g.out_f32 + (size_t)row * g.ldo + cc;
-#pragma unroll
-          for (int i = 0; i < 16; ++i) atomicAdd(o + i, vv[i]);
-        } else {  // kEpiReluMask: gradient through the ReLU of a stored activation
-          const __nv_bfloat16 *ref = g.relu_ref + (size_t)row * g.ldr + cc;
-          __nv_bfloat16 *o = g.out_bf16 + (size_t)row * g.ldo + cc;
-#pragma unroll
-          for (int i = 0; i < 16; i += 2) {
-            const float a = __bfloat162float(ref[i]) > 0.0f ? vv[i] : 0.0f;
-            const float b = __bfloat162float(ref[i + 1]) > 0.0f ? vv[i + 1] : 0.0f;
-            *reinterpret_cast<__nv_bfloat162 *>(o + i) = __floats2bfloat162_rn(a, b);
+          float *o = g.out_f32 + (size_t)row * g.ldo + col;
+          atomicAdd(o, x.x);
+          atomicAdd(o + 1, x.y);
+          atomicAdd(o + 2, x.z);
+          atomicAdd(o + 3, x.w);
+        } else {
+          float a = x.x, b = x.y, c = x.z, e = x.w;
+          if (g.mode == kEpiReluMask) {  // gradient through the ReLU of the stored activation
+            const uint2 rq = rref[rr >> 1];
+            const __nv_bfloat162 r01 = *reinterpret_cast<const __nv_bfloat162 *>(&rq.x);
+            const __nv_bfloat162 r23 = *reinterpret_cast<const __nv_bfloat162 *>(&rq.y);
+            a = __low2float(r01) > 0.0f ? a : 0.0f;
+            b = __high2float(r01) > 0.0f ? b : 0.0f;
+            c = __low2float(r23) > 0.0f ? c : 0.0f;
+            e = __high2float(r23) > 0.0f ? e : 0.0f;
           }
+          const __nv_bfloat162 o01 = __floats2bfloat162_rn(a, b), o23 = __floats2bfloat162_rn(c, e);
+          uint2 oq;
+          oq.x = *reinterpret_cast<const uint32_t *>(&o01);
+          oq.y = *reinterpret_cast<const uint32_t *>(&o23);
+          *reinterpret_cast<uint2 *>(g.out_bf16 + (size_t)row * g.ldo + col) = oq;
         }
       }
+      __syncwarp();
     }
   }
   if (fail_flag && tid == 0 && g.err) atomicExch(g.err, 1);
@@ -692,14 +701,13 @@ bool tile_map(CUtensorMap *map, const __nv_bfloat16 *base, int rows, int K, int 
 }  // namespace
 
 cudaError_t gemm(const GemmArgs &g, int splits, cudaStream_t st) {
-  if (g.N < 16 || g.N > 256 || (g.N & 15) || (g.K & 15) || (g.lda & 7) || (g.ldb & 7) || splits < 1)
+  if (g.N < 16 || g.N > 256 || (g.N & 15) || (g.K & 15) || (g.lda & 7) || (g.ldb & 7) || (g.ldo & 3) ||
+      (g.mode == kEpiReluMask && (g.ldr & 3)) || splits < 1)
     return cudaErrorInvalidValue;
-  static std::once_flag attr_once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
-  });
-  if (attr_err != cudaSuccess) return attr_err;
+  // set on every call: the attribute belongs to the current device
+  if (cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
+      e != cudaSuccess)
+    return e;
   alignas(64) CUtensorMap ta, tb;
   if (!tile_map(&ta, g.A, g.M, g.K, g.lda, kTileM) || !tile_map(&tb, g.B, g.N, g.K, g.ldb, g.N))
     return cudaErrorInvalidValue;
@@ -715,12 +723,9 @@ cudaError_t gemm(const GemmArgs &g, int splits, cudaStream_t st) {
 
 cudaError_t forward(const FwdArgs &g, const __nv_bfloat16 *const w[4], cudaStream_t st) {
   if (g.Mp <= 0 || (g.Mp % kTileM) || !g.x0 || !g.z) return cudaErrorInvalidValue;
-  static std::once_flag attr_once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
-  });
-  if (attr_err != cudaSuccess) return attr_err;
+  if (cudaError_t e = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+      e != cudaSuccess)
+    return e;
   alignas(64) FwdTmaps tm;
   for (int l = 0; l < kFwdLayers; ++l) {
     const int K = l == 0 ? 16 : 256;
