@@ -65,6 +65,12 @@ typedef enum {
   QP_EINFEASIBLE = 6   /* decode: the state is not a one-hot permutation   */
 } qp_status;
 
+/* Every call that fails returns its status before launching any kernel on a
+ * buffer it could not allocate, and leaves the handle usable.  Failure
+ * injection for tests: with the environment variable QPATH_FAIL_ALLOC = N the
+ * library's next N device allocations succeed and every later one fails
+ * (QP_ENOMEM), until the variable changes or is removed. */
+
 typedef struct qp_handle qp_handle;
 
 /* A grid field (Section II).  free_mask[r*cols + c] = 1 marks a cell to

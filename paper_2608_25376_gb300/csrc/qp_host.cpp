@@ -40,6 +40,31 @@ qp_status fail(qp_status s, const char *fmt, ...) {
   return s;
 }
 
+}  // namespace host
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+  static std::mutex mu;
+  static std::string seen;
+  static long left = -1;  // allocations before injected failures start; -1 = none
+  {
+    const char *env = std::getenv("QPATH_FAIL_ALLOC");
+    const std::string v = env ? env : "";
+    std::lock_guard<std::mutex> lk(mu);
+    if (v != seen) {
+      seen = v;
+      left = v.empty() ? -1 : std::max(0L, std::strtol(v.c_str(), nullptr, 10));
+    }
+    if (left == 0) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+    if (left > 0) --left;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+namespace host {
+
 bool is_device_ptr(const void *p) {
   if (!p) return false;
   cudaPointerAttributes at;

@@ -52,7 +52,7 @@ struct DevBuf {
   qp_status ensure(size_t want) {
     if (want <= bytes) return QP_OK;
     release();
-    cudaError_t e = cudaMalloc(&p, want);
+    cudaError_t e = dev_malloc(&p, want);
     if (e != cudaSuccess) {
       cudaGetLastError();
       p = nullptr;

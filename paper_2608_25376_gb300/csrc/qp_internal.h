@@ -144,4 +144,10 @@ bool schedule_lookup(const qp_schedule &sc, DeviceSchedule *out, std::shared_ptr
 qp_status set_error(qp_status s, const char *msg);
 bool device_pointer(const void *p);
 
+// Every device allocation of the library.  Fault injection for tests: when
+// the environment variable QPATH_FAIL_ALLOC holds N, the next N allocations
+// (counted from the moment the value was first seen) succeed and every later
+// one fails with cudaErrorMemoryAllocation, until the value changes.
+cudaError_t dev_malloc(void **p, size_t bytes);
+
 }  // namespace qp

@@ -35,7 +35,7 @@ struct Buf {
     if (p) cudaFree(p);
     p = nullptr;
     bytes = 0;
-    if (cudaMalloc(&p, want) != cudaSuccess) {
+    if (dev_malloc(&p, want) != cudaSuccess) {
       cudaGetLastError();
       p = nullptr;
       return false;
@@ -96,6 +96,7 @@ size_t n_params() {
 
 qp_status ensure_rows(qp_ws *m, int Mp) {
   if (Mp <= m->cap) return QP_OK;
+  m->cap = 0;  // a failed growth below leaves some buffers empty: check them all next time
   WS_ALLOC(m->x0, (size_t)Mp * kIn * 2);
   for (int i = 0; i < 3; ++i) {
     WS_ALLOC(m->h[i], (size_t)Mp * kHid * 2);
