@@ -445,6 +445,18 @@ qp_status qp_ws_infer(qp_ws *ws, const qp_field *field, const int32_t *d, uint8_
  * long it waited, from the SM clock.  The context stays usable. */
 qp_status qp_selftest_wait(int32_t *timed_out, double *waited_ms);
 
+/* Device bounds checks (no counterpart in the paper; the substitute for a
+ * memory checker).  The checked build of the library (compiled with
+ * QP_DEVICE_CHECKS=1) tests, before the access, every index of the sweep and
+ * repair kernels' threshold-table, distance-row, spin-word, row-of-S and
+ * hot-cell reads and writes; a failed check records (site << 24) | (index mod
+ * 2^24) and the access goes to element 0 instead, so it cannot leave its
+ * array.  *enabled = 1 in the checked build, 0 in the release build (which
+ * compiles no checks).  *first_failure = the first failure since the last
+ * call, 0 = none; the call clears it.  Sites: 1 threshold table, 2 distance
+ * row, 3 spin word, 4 row of S, 5 repair distance, 6 hot-cell list. */
+qp_status qp_device_checks(int32_t *enabled, uint32_t *first_failure);
+
 /* Free a handle and its device memory (NULL is ignored). */
 void qp_destroy(qp_handle *h);
 

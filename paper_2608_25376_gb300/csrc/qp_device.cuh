@@ -5,10 +5,45 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#ifndef QP_DEVICE_CHECKS
+#define QP_DEVICE_CHECKS 0
+#endif
+
 namespace qp {
 namespace dev {
 
 constexpr unsigned kFull = 0xffffffffu;
+
+// Device bounds checks, compiled in only with QP_DEVICE_CHECKS=1 (the checked
+// build of the library).  QP_IX(i, n, site) is i when 0 <= i < n; otherwise
+// the first failure of the translation unit's kernels is recorded as
+// (site << 24) | (i mod 2^24) and the access goes to element 0, so a wrong
+// index cannot reach memory outside its array.  Sites: 1 threshold table,
+// 2 distance row, 3 spin word, 4 row of S, 5 repair distance, 6 hot-cell list.
+// In the release build QP_IX(i, n, site) is i.
+#if QP_DEVICE_CHECKS
+static __device__ unsigned int g_check_word;
+__device__ __forceinline__ long long check_ix(long long i, long long n, unsigned site) {
+  if (i >= 0 && i < n) return i;
+  atomicCAS(&g_check_word, 0u, (site << 24) | ((unsigned)i & 0xFFFFFFu));
+  return 0;
+}
+#define QP_IX(i, n, site) ((decltype(i))::qp::dev::check_ix((long long)(i), (long long)(n), (site)))
+// Host accessor of the translation unit's word: returns it and clears it.
+#define QP_CHECK_ACCESSOR(fn)                                                        \
+  uint32_t fn() {                                                                    \
+    unsigned v = 0;                                                                  \
+    if (cudaMemcpyFromSymbol(&v, ::qp::dev::g_check_word, sizeof v) != cudaSuccess) \
+      return 0xFFFFFFFFu;                                                            \
+    const unsigned z = 0;                                                            \
+    cudaMemcpyToSymbol(::qp::dev::g_check_word, &z, sizeof z);                      \
+    return v;                                                                        \
+  }
+#else
+#define QP_IX(i, n, site) (i)
+#define QP_CHECK_ACCESSOR(fn) \
+  uint32_t fn() { return 0; }
+#endif
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of the 4x32 S-box with
 // the key bumped by the Weyl constants between rounds.
@@ -49,12 +84,12 @@ constexpr float kAcceptMargin = 1.0f / 4096.0f;
 // v(1 -/+ margin) -/+ 2 around the float estimate the answer is the table's
 // (u < v(1-m) - 2 implies u < V - 1, hence u < floor(V); u > v(1+m) + 2
 // implies u >= floor(V)); inside the band the table itself is read.
-__device__ __forceinline__ bool accept_draw(uint32_t u, int dE, float c, const uint32_t *thr) {
+__device__ __forceinline__ bool accept_draw(uint32_t u, int dE, float c, const uint32_t *thr, int len) {
   const float v = exp2f(32.0f - (float)dE * c);
   const float uf = __uint2float_rn(u);
   if (uf < fmaf(v, -kAcceptMargin, v) - 2.0f) return true;
   if (uf > fmaf(v, kAcceptMargin, v) + 2.0f) return false;
-  return u < __ldg(thr + dE);
+  return u < __ldg(thr + QP_IX(dE, len, 1));
 }
 
 // ---- bulk copies global -> shared with mbarrier completion

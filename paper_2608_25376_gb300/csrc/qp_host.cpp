@@ -439,6 +439,19 @@ extern "C" qp_status qp_export_dense(const qp_handle *h, int32_t *S_out) {
   return QP_OK;
 }
 
+extern "C" qp_status qp_device_checks(int32_t *enabled, uint32_t *first_failure) {
+  g_err.clear();
+  if (!enabled || !first_failure) return fail(QP_EINVAL, "enabled and first_failure are required");
+  *enabled = qp::chk::enabled();
+  uint32_t w = 0;
+  for (uint32_t (*take)() : {qp::chk::rows, qp::chk::kernels, qp::chk::group, qp::chk::repair}) {
+    const uint32_t v = take();
+    if (!w) w = v;
+  }
+  *first_failure = w;
+  return QP_OK;
+}
+
 extern "C" qp_status qp_thresholds(const qp_schedule *sc, int32_t sweep, uint32_t *out, int32_t cap,
                                    int32_t *len_out) {
   g_err.clear();

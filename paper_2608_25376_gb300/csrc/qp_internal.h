@@ -150,4 +150,15 @@ bool device_pointer(const void *p);
 // one fails with cudaErrorMemoryAllocation, until the value changes.
 cudaError_t dev_malloc(void **p, size_t bytes);
 
+// Device bounds checks of the checked build (QP_DEVICE_CHECKS=1): each
+// returns, and clears, the first failed check of its translation unit's
+// kernels, (site << 24) | index, 0 = none; always 0 in the release build.
+namespace chk {
+uint32_t kernels();
+uint32_t rows();
+uint32_t group();
+uint32_t repair();
+int32_t enabled();
+}  // namespace chk
+
 }  // namespace qp

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32)
           xn = (st[k0 >> 5] >> (k0 & 31)) & 0xFu;
           int f[4] = {0, 0, 0, 0};
           for (int h = 0; h < nh; ++h) {
-            const DT *drow = d + (size_t)hot[h] * Cp;
+            const DT *drow = d + (size_t)QP_IX((int)hot[h], C, 6) * Cp;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               const int i = k0 + j - kb;
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32)
           }
 #pragma unroll
           for (int j = 0; j < 4; ++j)
-            if (((need >> j) & 1) && dev::accept_draw(word_of(u, j), dE[j], cT, thr)) accm |= 1 << j;
+            if (((need >> j) & 1) && dev::accept_draw(word_of(u, j), dE[j], cT, thr, len)) accm |= 1 << j;
           const uint32_t bal = __ballot_sync(kFull, accm != 0);
           if (bal == 0) break;
           const int L = __ffs(bal) - 1;
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_sweep_dense(const Dens
       while (wd) {
         const int l = ((w0 + L) << 5) + __ffs(wd) - 1;
         wd &= wd - 1;
-        add_row(h, S + (size_t)l * np, np, 1, lane);
+        add_row(h, S + (size_t)QP_IX(l, n, 4) * np, np, 1, lane);
         __syncwarp();
         if (lane == 0) h[l] -= ld_elem(S + (size_t)l * np + l, false);
         __syncwarp();
@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_sweep_dense(const Dens
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-          if (((need >> j) & 1) && dev::accept_draw(word_of(u, j), dE[j], cT, thr)) accm |= 1 << j;
+          if (((need >> j) & 1) && dev::accept_draw(word_of(u, j), dE[j], cT, thr, len)) accm |= 1 << j;
         const uint32_t bal = __ballot_sync(kFull, accm != 0);
         if (bal == 0) break;
         const int L = __ffs(bal) - 1;
@@ -533,7 +533,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_sweep_dense(const Dens
         int32_t skk;
         if (BULK) {
           __syncwarp();
-          if (lane == 0) dev::bulk_copy(dev::smem_addr(stage), S + (size_t)k * np, (uint32_t)(sizeof(ST) * np), mbar);
+          if (lane == 0)
+            dev::bulk_copy(dev::smem_addr(stage), S + (size_t)QP_IX(k, n, 4) * np, (uint32_t)(sizeof(ST) * np), mbar);
           const bool done = __all_sync(kFull, dev::mbar_wait_bounded(mbar, parity));
           parity ^= 1u;
           if (!done) {
@@ -548,7 +549,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_sweep_dense(const Dens
           add_row_staged(h, stage, np, dlt, lane);
           skk = (int32_t)stage[k];
         } else {
-          add_row(h, S + (size_t)k * np, np, dlt, lane);
+          add_row(h, S + (size_t)QP_IX(k, n, 4) * np, np, dlt, lane);
           skk = 0;
         }
         __syncwarp();
@@ -769,4 +770,11 @@ cudaError_t launch_decode(const uint8_t *states, int32_t R, int32_t C, const int
   return cudaGetLastError();
 }
 
+}  // namespace qp
+
+namespace qp {
+namespace chk {
+QP_CHECK_ACCESSOR(kernels)
+int32_t enabled() { return QP_DEVICE_CHECKS; }
+}  // namespace chk
 }  // namespace qp

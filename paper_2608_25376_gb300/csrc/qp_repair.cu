@@ -85,7 +85,7 @@ __global__ void k_repair(const uint8_t *__restrict__ states, int R, int C, int s
   // greedy fix
   for (int t = 1; t < C; ++t) {
     const int prev = path[t - 1];
-    const int32_t *drow = d + (size_t)prev * C;
+    const int32_t *drow = d + (size_t)QP_IX(prev, C, 5) * C;
     const uint8_t *xr = x + (size_t)t * C;
     uint64_t best_hot = ~0ull, best_any = ~0ull;
     int hot = 0;
@@ -113,7 +113,7 @@ __global__ void k_repair(const uint8_t *__restrict__ states, int R, int C, int s
   }
 
   // 2-opt
-  for (int t = lane; t + 1 < C; t += 32) edge[t] = d[(size_t)path[t] * C + path[t + 1]];
+  for (int t = lane; t + 1 < C; t += 32) edge[t] = d[QP_IX((size_t)path[t] * C + path[t + 1], (size_t)C * C, 5)];
   __syncwarp();
   bool changed = false;
   bool moved = true;
@@ -129,10 +129,10 @@ __global__ void k_repair(const uint8_t *__restrict__ states, int R, int C, int s
         if (j < C) {
           const int pj = path[j];
           int64_t old = edge[i - 1];
-          n1 = d[(size_t)a * C + pj];
+          n1 = d[QP_IX((size_t)a * C + pj, (size_t)C * C, 5)];
           if (j + 1 < C) {
             old += edge[j];
-            n2 = d[(size_t)b * C + path[j + 1]];
+            n2 = d[QP_IX((size_t)b * C + path[j + 1], (size_t)C * C, 5)];
           }
           imp = (int64_t)n1 + n2 < old;
         }
@@ -161,7 +161,7 @@ __global__ void k_repair(const uint8_t *__restrict__ states, int R, int C, int s
   long long L = 0;
   for (int t = lane; t < C; t += 32) {
     out[t] = path[t];
-    if (t + 1 < C) L += d[(size_t)path[t] * C + path[t + 1]];
+    if (t + 1 < C) L += d[QP_IX((size_t)path[t] * C + path[t + 1], (size_t)C * C, 5)];
   }
   L = dev::warp_sum64(L);
   if (lane == 0) {
@@ -188,4 +188,10 @@ cudaError_t launch_repair(const uint8_t *states, int32_t R, int32_t C, int32_t s
   return cudaGetLastError();
 }
 
+}  // namespace qp
+
+namespace qp {
+namespace chk {
+QP_CHECK_ACCESSOR(repair)
+}  // namespace chk
 }  // namespace qp

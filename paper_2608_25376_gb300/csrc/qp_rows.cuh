@@ -8,9 +8,11 @@ __host__ __device__ constexpr size_t align16r(size_t x) { return (x + 15) & ~siz
 
 // d modes: 0 = global memory (DT), 1 = shared memory (DT), 2 = shared memory widened to int32
 template <typename DT, int DMODE>
-__device__ __forceinline__ void drow4(const void *d, int Cp, int h, int i, bool ok, int (&v)[4]) {
+__device__ __forceinline__ void drow4(const void *d, int Cp, int C, int h, int i, bool ok, int (&v)[4]) {
   v[0] = v[1] = v[2] = v[3] = 0;
   if (!ok) return;
+  h = QP_IX(h, C, 2);  // the four entries i..i+3 < Cp of row h
+  i = QP_IX(i, Cp - 3, 2);
   if (DMODE == 2) {
     const int4 q = *reinterpret_cast<const int4 *>(static_cast<const int *>(d) + (size_t)h * Cp + i);
     v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
@@ -35,7 +37,7 @@ __device__ __forceinline__ void add_drow(const void *d, int Cp, int C, int h, in
   for (int c = 0; c < NCH; ++c) {
     const int i = 128 * c + 4 * lane;
     int v[4];
-    drow4<DT, DMODE>(d, Cp, h, i, i < C, v);
+    drow4<DT, DMODE>(d, Cp, C, h, i, i < C, v);
 #pragma unroll
     for (int j = 0; j < 4; ++j) F[c][j] += dlt * v[j];
   }
@@ -46,7 +48,7 @@ __device__ __forceinline__ void set_drow(const void *d, int Cp, int C, int h, in
 #pragma unroll
   for (int c = 0; c < NCH; ++c) {
     const int i = 128 * c + 4 * lane;
-    drow4<DT, DMODE>(d, Cp, h, i, i < C, F[c]);
+    drow4<DT, DMODE>(d, Cp, C, h, i, i < C, F[c]);
   }
 }
 
@@ -156,7 +158,7 @@ __device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         // dE >= dq gives thr[dE] <= thr[dq] = Q, so u >= Q rejects outright
-        if (((need >> j) & 1) && (dE[j] < dq || uw[j] < Q) && accept_draw(uw[j], dE[j], cT, thr))
+        if (((need >> j) & 1) && (dE[j] < dq || uw[j] < Q) && accept_draw(uw[j], dE[j], cT, thr, len))
           accm |= 1 << j;
       }
     }
@@ -180,7 +182,7 @@ __device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int
       for (int j = 0; j < 4; ++j)
         if (j == jj) tAc[j] += dlt * twoA;
       xnc ^= 1 << jj;
-      row[4 * c + (L >> 3)] ^= 1u << (4 * (L & 7) + jj);
+      row[QP_IX(4 * c + (L >> 3), (C + 31) >> 5, 3)] ^= 1u << (4 * (L & 7) + jj);
     }
     add_drow<DT, NCH, DMODE>(d, Cp, C, 128 * c + 4 * L + jj, lane, dlt, Cu);
     cand &= lane < L ? 0 : (lane > L ? 0xF : (0xF << (jj + 1)) & 0xF);

@@ -37,10 +37,12 @@ __host__ __device__ constexpr size_t al16(size_t x) { return (x + 15) & ~size_t(
 // 8 consecutive entries of row h of d, from column i (a multiple of 8).
 // DMODE 0: global (DT), 1: shared (DT), 2: shared widened to int32.
 template <typename DT, int DMODE>
-__device__ __forceinline__ void drow8(const void *d, int Cp, int h, int i, bool ok, int (&v)[V]) {
+__device__ __forceinline__ void drow8(const void *d, int Cp, int C, int h, int i, bool ok, int (&v)[V]) {
 #pragma unroll
   for (int j = 0; j < V; ++j) v[j] = 0;
   if (!ok) return;
+  h = QP_IX(h, C, 2);  // the eight entries i..i+7 < Cp of row h
+  i = QP_IX(i, Cp - 7, 2);
   if (DMODE == 2) {
     const int4 *p = reinterpret_cast<const int4 *>(static_cast<const int *>(d) + (size_t)h * Cp + i);
     const int4 q0 = p[0], q1 = p[1];
@@ -66,7 +68,7 @@ __device__ __forceinline__ void drow8(const void *d, int Cp, int h, int i, bool 
 template <typename DT, int DMODE>
 __device__ __forceinline__ void add_drow8(const void *d, int Cp, int C, int h, int ib, int dlt, int (&F)[V]) {
   int v[V];
-  drow8<DT, DMODE>(d, Cp, h, ib, ib < C, v);
+  drow8<DT, DMODE>(d, Cp, C, h, ib, ib < C, v);
 #pragma unroll
   for (int j = 0; j < V; ++j) F[j] += dlt * v[j];
 }
@@ -344,7 +346,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_sweep_group(const Stru
               if ((need >> j) & 1) {
                 const int kb = (delta + j) >> 2, w = (delta + j) & 3;
                 const uint32_t u = kb == 0 ? word_of(u0, w) : (kb == 1 ? word_of(u1, w) : word_of(u2, w));
-                if (accept_draw(u, dE[j], cT, thr)) accm |= 1 << j;
+                if (accept_draw(u, dE[j], cT, thr, len)) accm |= 1 << j;
               }
             }
           }
@@ -469,4 +471,10 @@ cudaError_t launch_group(const StructArgs &a_in, bool d_i16, int W, cudaStream_t
   return G == 4 ? launch_g2<int32_t, 4>(a, dmode, W, smem, st) : launch_g2<int32_t, 2>(a, dmode, W, smem, st);
 }
 
+}  // namespace qp
+
+namespace qp {
+namespace chk {
+QP_CHECK_ACCESSOR(group)
+}  // namespace chk
 }  // namespace qp

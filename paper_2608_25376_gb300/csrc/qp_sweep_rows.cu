@@ -352,3 +352,9 @@ cudaError_t launch_rows(const StructArgs &a_in, bool d_i16, int W, cudaStream_t 
 }
 
 }  // namespace qp
+
+namespace qp {
+namespace chk {
+QP_CHECK_ACCESSOR(rows)
+}  // namespace chk
+}  // namespace qp

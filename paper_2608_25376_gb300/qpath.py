@@ -31,7 +31,8 @@ SYMBOLS = ["qp_build_qubo", "qp_build_from_dense", "qp_qubo_info", "qp_export_de
            "qp_batch_run", "qp_batch_info", "qp_batch_destroy", "qp_anneal_batch", "qp_decode_path",
            "qp_decode_batch", "qp_repair_batch", "qp_repair_path", "qp_anneal_timed", "qp_anneal_pt", "qp_ws_create", "qp_ws_destroy", "qp_ws_param_count", "qp_ws_get_params",
            "qp_ws_set_params", "qp_ws_features", "qp_ws_forward", "qp_ws_set_forward_mode", "qp_ws_grads", "qp_ws_train_step",
-           "qp_ws_decode", "qp_ws_decode_walk", "qp_ws_infer", "qp_selftest_wait", "qp_destroy", "qp_last_error"]
+           "qp_ws_decode", "qp_ws_decode_walk", "qp_ws_infer", "qp_selftest_wait", "qp_device_checks", "qp_destroy",
+           "qp_last_error"]
 
 
 class QpError(RuntimeError):
@@ -74,7 +75,8 @@ class qp_anneal_opts(ct.Structure):
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """The library to load: QPATH_LIBRARY when set (e.g. the checked build), else the release build."""
+    return os.environ.get("QPATH_LIBRARY") or _build.LIB
 
 
 def lib():
@@ -115,6 +117,7 @@ def lib():
                 "qp_ws_decode_walk": [vp, i32, i32, i32, vp, vp, vp],
                 "qp_ws_infer": [vp, P(qp_field), vp, vp, vp, vp],
                 "qp_selftest_wait": [P(i32), P(ct.c_double)],
+                "qp_device_checks": [P(i32), P(ct.c_uint32)],
                 "qp_decode_path": [vp, vp, vp, vp],
                 "qp_decode_batch": [vp, i32, vp, vp, vp, vp],
                 "qp_repair_batch": [vp, i32, vp, i32, vp, vp, vp, vp],
@@ -522,3 +525,10 @@ def qp_selftest_wait() -> dict:
     t, w = ct.c_int32(), ct.c_double()
     _check(lib().qp_selftest_wait(ct.byref(t), ct.byref(w)))
     return {"timed_out": t.value, "waited_ms": w.value}
+
+
+def qp_device_checks():
+    """(enabled, first_failure) of the loaded library's device bounds checks; clears the record."""
+    en, w = ct.c_int32(), ct.c_uint32()
+    _check(lib().qp_device_checks(ct.byref(en), ct.byref(w)))
+    return bool(en.value), int(w.value)
