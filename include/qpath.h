@@ -120,7 +120,8 @@ enum { QP_ANNEAL_SKIP_SETTLED = 1 };
 
 typedef struct {
   int32_t kernel;            /* QP_KERNEL_*; AUTO = structured when built     */
-  int32_t replicas_per_cta;  /* warps (= replicas) per CTA; 0 = tuned default */
+  int32_t replicas_per_cta;  /* warps (= replicas) per CTA; 0 = chosen to keep
+                                the most chains resident at once (occupancy) */
   int32_t replica_offset;    /* global index of replica 0 (its RNG stream)    */
   int64_t *accepts_out;      /* optional [R]: accepted flips per replica      */
   int32_t flags;             /* QP_ANNEAL_* bits                              */

@@ -477,13 +477,14 @@ namespace host {
 qp_status launch_structured_auto(qp_handle *h, StructArgs &a, int W, bool allow_rows, cudaStream_t st,
                                  LaunchInfo *info) {
   if (allow_rows) {
-    int Wr = W;
+    int Wr = W > 0 ? W : rows_auto_warps(h->C, h->d_i16, a.R);
     while (Wr > 1 && !rows_supported(h->C, h->d_i16, Wr)) --Wr;
     if (rows_supported(h->C, h->d_i16, Wr)) {
       QP_CU(launch_rows(a, h->d_i16, Wr, st, info));
       return QP_OK;
     }
   }
+  if (W <= 0) W = 4;
   a.nw_pad = (int32_t)structured_gstate_words(h->C);
   const bool want_smem = structured_state_fits_smem(h->C, h->d_i16, W) &&
                          4 * structured_gstate_words(h->C) <= 8 * 1024;
@@ -567,7 +568,8 @@ extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc
       QP_CU(launch_group(a, h->d_i16, Wg, st, &info));
       goto launched;
     }
-    QP_TRY(launch_structured_auto(h, a, W, kernel != QP_KERNEL_STRUCTURED_FLAT, st, &info));
+    // replicas per CTA as asked, else chosen for the most resident chains
+    QP_TRY(launch_structured_auto(h, a, o.replicas_per_cta, kernel != QP_KERNEL_STRUCTURED_FLAT, st, &info));
   } else {
     int W = o.replicas_per_cta ? o.replicas_per_cta : 4;
     while (W > 1 && !dense_h_fits_smem(h->n, h->path ? h->C : 0, W)) --W;

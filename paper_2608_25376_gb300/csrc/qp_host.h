@@ -130,6 +130,7 @@ namespace qp {
 namespace host {
 // The structured sweep of a.R replicas: the row kernel when allowed and the
 // field fits it, else the flat kernel.
+// W = replicas per CTA, 0 = chosen from the occupancy (row kernel) or 4 (flat kernel)
 qp_status launch_structured_auto(qp_handle *h, StructArgs &a, int W, bool allow_rows, cudaStream_t st,
                                  LaunchInfo *info);
 }  // namespace host

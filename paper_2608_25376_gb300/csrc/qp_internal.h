@@ -86,6 +86,9 @@ size_t structured_gstate_words(int C);  // nw_pad for the global-state layout
 bool structured_state_fits_smem(int C, bool d_i16, int warps_per_cta);
 // Row-parallel structured kernel (qp_sweep_rows.cu), fields of up to 512 cells.
 bool rows_supported(int C, bool d_i16, int warps_per_cta);
+// Replicas per CTA for the row kernel that keep the most chains resident on
+// the GPU at once (R replicas in all); memoised per device and shape.
+int rows_auto_warps(int C, bool d_i16, int R);
 cudaError_t launch_rows(const StructArgs &a, bool d_i16, int warps_per_cta, cudaStream_t st,
                         LaunchInfo *info);
 // Batched persistent launch (qp_sweep_rows.cu): fields[] per field, units[]

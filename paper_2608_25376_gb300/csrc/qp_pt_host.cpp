@@ -143,7 +143,7 @@ extern "C" qp_status qp_anneal_pt(qp_handle *h, int32_t G, const qp_pt_schedule 
     a.sweep_end = (e + 1) * I;
     a.init = e == 0 ? init_d : cur;
     a.states_out = nxt;
-    QP_TRY(launch_structured_auto(h, a, 4, true, st, &info));
+    QP_TRY(launch_structured_auto(h, a, 0, true, st, &info));
     x.phase = e & 1;
     x.round = e;
     QP_CU(launch_pt_exchange(x, st));

@@ -29,6 +29,9 @@
 // Most draws are rejected by two integer compares (u >= thr[dq] with
 // dq ~ 8 T ln 2 and dE >= dq) before the float estimate of exp(-dE/T).
 #include <climits>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "qp_device.cuh"
 #include "qp_internal.h"
@@ -325,13 +328,87 @@ cudaError_t launch_batch(const StructArgs *fields, const int2 *units, int n_unit
   return cudaGetLastError();
 }
 
+namespace {
+
+int rows_dmode(int C, bool d_i16, int W) {
+  if (rows_smem(C, d_i16, W, 2) <= kSmemLimitRows) return 2;
+  if (rows_smem(C, d_i16, W, 1) <= kSmemLimitRows) return 1;
+  return 0;
+}
+
+template <typename DT, int NCH, int DMODE>
+cudaError_t occ_r(int W, size_t smem, int *blocks) {
+  auto k = k_sweep_rows<DT, NCH, DMODE>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, W * 32, smem);
+}
+
+template <typename DT, int NCH>
+cudaError_t occ_r2(int dmode, int W, size_t smem, int *blocks) {
+  if (dmode == 2) return occ_r<DT, NCH, 2>(W, smem, blocks);
+  if (dmode == 1) return occ_r<DT, NCH, 1>(W, smem, blocks);
+  return occ_r<DT, NCH, 0>(W, smem, blocks);
+}
+
+// CTAs of W replicas that fit on one SM at once (0 when none or on error).
+int rows_blocks_per_sm(int C, bool d_i16, int W) {
+  const int dmode = rows_dmode(C, d_i16, W);
+  const size_t smem = rows_smem(C, d_i16, W, dmode);
+  const int NCH = C <= 128 ? 1 : (C <= 256 ? 2 : 4);
+  int b = 0;
+  cudaError_t e;
+  if (d_i16) e = NCH == 1 ? occ_r2<int16_t, 1>(dmode, W, smem, &b)
+                          : (NCH == 2 ? occ_r2<int16_t, 2>(dmode, W, smem, &b) : occ_r2<int16_t, 4>(dmode, W, smem, &b));
+  else e = NCH == 1 ? occ_r2<int32_t, 1>(dmode, W, smem, &b)
+                    : (NCH == 2 ? occ_r2<int32_t, 2>(dmode, W, smem, &b) : occ_r2<int32_t, 4>(dmode, W, smem, &b));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return b;
+}
+
+}  // namespace
+
+int rows_auto_warps(int C, bool d_i16, int R) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 4;
+  }
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, bool, int>, int> memo;
+  const auto key = std::make_tuple(dev, C, d_i16, R);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = memo.find(key);
+    if (it != memo.end()) return it->second;
+  }
+  // the most replicas resident at once (a sequential chain per warp: the
+  // kernel is latency-bound, so resident chains are its throughput); among
+  // equals the default of 4 replicas per CTA, then the smaller CTA
+  int best_w = 4;
+  long long best = -1;
+  for (int W = 1; W <= kMaxWarpsPerCta; ++W) {
+    if (!rows_supported(C, d_i16, W)) continue;
+    const long long resident = std::min<long long>(R, (long long)sms * rows_blocks_per_sm(C, d_i16, W) * W);
+    if (resident > best || (resident == best && W == 4)) {
+      best = resident;
+      best_w = W;
+    }
+  }
+  if (!rows_supported(C, d_i16, best_w)) best_w = 1;
+  std::lock_guard<std::mutex> lk(mu);
+  memo[key] = best_w;
+  return best_w;
+}
+
 cudaError_t launch_rows(const StructArgs &a_in, bool d_i16, int W, cudaStream_t st, LaunchInfo *info) {
   StructArgs a = a_in;
   a.nw_pad = (int32_t)rows_state_words(a.C);
   if (!rows_supported(a.C, d_i16, W)) return cudaErrorInvalidValue;
-  int dmode = 0;
-  if (rows_smem(a.C, d_i16, W, 2) <= kSmemLimitRows) dmode = 2;
-  else if (rows_smem(a.C, d_i16, W, 1) <= kSmemLimitRows) dmode = 1;
+  const int dmode = rows_dmode(a.C, d_i16, W);
   const size_t smem = rows_smem(a.C, d_i16, W, dmode);
   if (smem > kSmemLimitRows) return cudaErrorInvalidValue;
   const int NCH = a.C <= 128 ? 1 : (a.C <= 256 ? 2 : 4);
