@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-warm-start", action="store_true")
     ap.add_argument("--no-paper-protocol", action="store_true")
     ap.add_argument("--no-replica-exchange", action="store_true")
+    ap.add_argument("--no-repair", action="store_true")
     ap.add_argument("--no-skip-settled", action="store_true")
     ap.add_argument("--no-other-configs", action="store_true")
     ap.add_argument("--replicas-per-cta", type=int, default=0)
@@ -376,6 +377,63 @@ def bench_paper_protocol():
             "grids": rows}
 
 
+def bench_repair(h, states, R, flush, stream):
+    """Repair (greedy fix + 2-opt to convergence) of the step's R final states
+    on the device, one warp per state; returns the timing and 8 states (host)
+    for the CPU reference."""
+    import torch
+    from paper_2608_25376_gb300 import qpath
+    C = h.info["C"]
+    paths = torch.zeros((R, C), dtype=torch.int32, device="cuda")
+    lens = torch.zeros(R, dtype=torch.int64, device="cuda")
+    stat = torch.zeros(R, dtype=torch.int32, device="cuda")
+    qpath.qp_repair_batch(h, R, states, -1, paths, lens, stat, stream=stream)
+    ts = []
+    for k in range(3):
+        flush.fill_(k)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        qpath.qp_repair_batch(h, R, states, -1, paths, lens, stat, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = statistics.mean(ts)
+    counts = torch.bincount(stat.long(), minlength=3).tolist()
+    return ({"value": R / (ms / 1e3), "unit": "states/s", "ms": ms, "states": R, "cells": C,
+             "passes": "2-opt until no move shortens the path",
+             "kept_shortened_fixed": counts[:3], "mean_length": float(lens.double().mean().item()),
+             "best_length": int(lens.min().item())},
+            states[:8].cpu().numpy())
+
+
+def cpu_other_rows(P, repair_states, with_pt):
+    """The CPU references of the repair and of replica exchange, as they stand,
+    on bounded samples of the same field."""
+    import oracle
+    from oracle import pt_ref, repair_ref
+    out = {}
+    if repair_states is not None:
+        dl = P.d.tolist()
+        t0 = time.perf_counter()
+        for x in repair_states:
+            repair_ref.repair(x.tolist(), dl, P.C, P.start_cell, -1)
+        dt = time.perf_counter() - t0
+        out["repair"] = {"value": len(repair_states) / dt, "unit": "states/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{len(repair_states)} of the step's final states, greedy fix + 2-opt to "
+                                   f"convergence, plain Python", "seconds": dt}
+    if with_pt:
+        G, M, I, rounds = 16, 32, 25, 10
+        t0 = time.perf_counter()
+        pt_ref.anneal_pt(P, G, M, 2.0, 1000.0, I, rounds, seed=1)
+        dt = time.perf_counter() - t0
+        out["replica_exchange"] = {"value": G * M * I * rounds * (P.C - 1) ** 2 / dt, "unit": UNIT,
+                                   "cores": os.cpu_count(), "kind": "oracle",
+                                   "sample": f"{G} groups x {M} levels, {rounds} rounds of {I} sweeps "
+                                             f"(the variant's ladder, fewer groups and rounds)",
+                                   "seconds": dt}
+    return out
+
+
 def bench_other_configs(flush, stream):
     """Throughput on the other workloads of the metric: the 4x4 grid as a dense
     QUBO (64 replicas x 2000 sweeps) and the 24x24 field with 15% obstacles
@@ -579,6 +637,10 @@ def run_ours(args):
     if not args.no_batch and rank == 0:
         line.setdefault("variants", {})["batched"] = bench_batch(args, flush, stream)
 
+    repair_sample = None
+    if not args.no_repair and rank == 0:
+        line.setdefault("variants", {})["repair"], repair_sample = bench_repair(h, states, R, flush, stream)
+
     if not args.no_other_configs and rank == 0:
         line.setdefault("variants", {})["other_configs"] = bench_other_configs(flush, stream)
 
@@ -624,6 +686,7 @@ def run_ours(args):
         import oracle
         P = oracle.Problem(f.rows, f.cols, f.free_mask, f.start)
         line["cpu_baseline"] = cpu_baseline(w, P)
+        line["cpu_baseline"]["other_rows"] = cpu_other_rows(P, repair_sample, not args.no_replica_exchange)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
