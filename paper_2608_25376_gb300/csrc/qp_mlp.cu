@@ -2,7 +2,10 @@
 // Linear(256)+ReLU -> Linear(256) step logits), trained with softmax
 // cross-entropy on the annealer's own best paths.
 //
-// Every matrix product (forward, dX = dY W, dW = dY^T X) runs on one tcgen05
+// The forward pass of all four layers runs as one kernel (k_mlp_forward, the
+// activations of a 128-cell tile kept in shared memory between layers).
+// Every other matrix product (dX = dY W, dW = dY^T X, and the forward as four
+// separate launches when asked) runs on one tcgen05
 // kernel: D[M x N] (+)= A[M x K] B[N x K]^T with bf16 operands (both K-major,
 // i.e. K contiguous) and fp32 accumulation in tensor memory.  A CTA owns a
 // 128 x N tile (N <= 256, multiple of 16) and walks K in chunks of 64 through
