@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--no-other-configs", action="store_true")
     ap.add_argument("--replicas-per-cta", type=int, default=0)
     ap.add_argument("--structured-kernel", default="rows", choices=["rows", "flat"])
-    ap.add_argument("--profile-case", default=None, choices=["rows", "flat", "dense", "mlp", "batch"],
+    ap.add_argument("--profile-case", default=None, choices=["rows", "flat", "dense", "mlp", "batch", "repair"],
                     help="run one warm-up and one measured launch of that kernel on a sub-range of "
                          "the workload (--sweep-window, --replicas), for ncu captures")
     ap.add_argument("--sweep-window", nargs=2, type=int, default=[0, 100])
@@ -724,6 +724,30 @@ def run_profile_case(args):
         print(json.dumps({"profile_case": "batch", "fields": len(hs), "replicas": R, "sweeps": [a, b], "ms": times,
                           "attempts": attempts}))
         bt.close()
+        return 0
+    if args.profile_case == "repair":
+        # the bench step's final states (1024 replicas of the 10x10 field after
+        # 5000 sweeps), then one warm-up and one measured repair of all of them
+        # (greedy fix + 2-opt to convergence)
+        w = inputs.WORKLOADS[args.workload]
+        h = qpath.qp_build_qubo(w["field"]())
+        n, C, R = h.info["n"], h.info["C"], w["replicas"]
+        st = torch.zeros((R, n), dtype=torch.uint8, device="cuda")
+        E = torch.zeros(R, dtype=torch.int64, device="cuda")
+        qpath.qp_anneal(h, R, qpath.schedule(w["n_sweeps"]), w["seed"], None, st, E,
+                        stream=torch.cuda.current_stream())
+        paths = torch.zeros((R, C), dtype=torch.int32, device="cuda")
+        lens = torch.zeros(R, dtype=torch.int64, device="cuda")
+        times = []
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            qpath.qp_repair_batch(h, R, st, -1, paths, lens, stream=torch.cuda.current_stream())
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        print(json.dumps({"profile_case": "repair", "workload": args.workload, "states": R, "cells": C,
+                          "ms": times, "mean_length": float(lens.double().mean().item())}))
         return 0
     if args.profile_case == "mlp":
         # one warm-up and one measured training step of the warm-start MLP on
