@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <memory>
+#include <mutex>
 #include <string>
 
 #include "qpath.h"
@@ -163,5 +164,11 @@ uint32_t group();
 uint32_t repair();
 int32_t enabled();
 }  // namespace chk
+
+// Held around every "set the kernel's dynamic shared-memory limit, then
+// launch (or query the occupancy)" pair whose size depends on the call, so
+// that calls from several host threads cannot launch under another call's
+// smaller limit.
+std::mutex &launch_mutex();
 
 }  // namespace qp

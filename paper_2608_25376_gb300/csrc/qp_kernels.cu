@@ -654,6 +654,7 @@ __global__ void k_decode(const uint8_t *states, int R, int C, const int32_t *d, 
 template <typename DT, bool SS, bool DS>
 cudaError_t launch_s(const StructArgs &a, int W, size_t smem, cudaStream_t st) {
   auto k = k_sweep_structured<DT, SS, DS>;
+  std::lock_guard<std::mutex> lk(launch_mutex());
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int blocks = (a.R + W - 1) / W;
@@ -664,6 +665,7 @@ cudaError_t launch_s(const StructArgs &a, int W, size_t smem, cudaStream_t st) {
 template <typename ST, bool HS, bool BULK>
 cudaError_t launch_d(const DenseArgs &a, int W, size_t smem, cudaStream_t st) {
   auto k = k_sweep_dense<ST, HS, BULK>;
+  std::lock_guard<std::mutex> lk(launch_mutex());
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int blocks = (a.R + W - 1) / W;
@@ -773,6 +775,11 @@ cudaError_t launch_decode(const uint8_t *states, int32_t R, int32_t C, const int
 }  // namespace qp
 
 namespace qp {
+std::mutex &launch_mutex() {
+  static std::mutex mu;
+  return mu;
+}
+
 namespace chk {
 QP_CHECK_ACCESSOR(kernels)
 int32_t enabled() { return QP_DEVICE_CHECKS; }

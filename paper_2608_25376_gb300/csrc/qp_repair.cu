@@ -182,6 +182,7 @@ cudaError_t launch_repair(const uint8_t *states, int32_t R, int32_t C, int32_t s
   while (W > 1 && W * per > 96 * 1024) W >>= 1;
   const size_t smem = W * per;
   if (smem > 96 * 1024) return cudaErrorInvalidValue;
+  std::lock_guard<std::mutex> lk(launch_mutex());
   cudaError_t e = cudaFuncSetAttribute(k_repair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_repair<<<(R + W - 1) / W, W * 32, smem, st>>>(states, R, C, start, d32, max_passes, paths, lengths, status);

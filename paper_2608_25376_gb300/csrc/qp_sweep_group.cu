@@ -429,6 +429,7 @@ size_t group_smem(int C, bool d_i16, int W, int G, int dmode) {
 template <typename DT, int DMODE, int G>
 cudaError_t launch_g(const StructArgs &a, int W, size_t smem, cudaStream_t st) {
   auto k = k_sweep_group<DT, DMODE, G>;
+  std::lock_guard<std::mutex> lk(launch_mutex());
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int reps_per_cta = W * G;

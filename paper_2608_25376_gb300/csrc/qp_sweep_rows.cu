@@ -257,6 +257,7 @@ constexpr size_t kSmemLimitRows = 227 * 1024;
 template <typename DT, int NCH, int DMODE>
 cudaError_t launch_r(const StructArgs &a, int W, size_t smem, cudaStream_t st) {
   auto k = k_sweep_rows<DT, NCH, DMODE>;
+  std::lock_guard<std::mutex> lk(launch_mutex());
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<(a.R + W - 1) / W, W * 32, smem, st>>>(a);
@@ -304,6 +305,7 @@ bool batch_supported(int Cmax, int W) {
 template <int NCH>
 static cudaError_t prep_batch(int W, size_t smem, int *blocks_per_sm) {
   auto k = k_sweep_batch<NCH>;
+  std::lock_guard<std::mutex> lk(launch_mutex());
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, W * 32, smem);
@@ -339,6 +341,7 @@ int rows_dmode(int C, bool d_i16, int W) {
 template <typename DT, int NCH, int DMODE>
 cudaError_t occ_r(int W, size_t smem, int *blocks) {
   auto k = k_sweep_rows<DT, NCH, DMODE>;
+  std::lock_guard<std::mutex> lk(launch_mutex());
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, W * 32, smem);
