@@ -131,6 +131,23 @@ def test_structured_multichunk(dev, orc, kname, kernel):
     assert_same(gpu_anneal(h, 3, 12, 3, kernel=kernel), ref)
 
 
+@pytest.mark.parametrize("kname,kernel", STRUCT_KERNELS)
+@pytest.mark.parametrize("rows,cols", [(8, 16), (3, 43), (16, 16), (1, 257)])
+def test_structured_at_chunk_boundaries(dev, orc, rows, cols, kname, kernel):
+    """C = 128, 129, 256, 257: the last field of one 128-column chunk per lane
+    and the first of two, the last of two and the first of four (here a single
+    257-cell row of the grid, so every step is along one line)."""
+    f = inputs.rect(rows, cols)
+    P = problem(orc, f)
+    assert P.C == rows * cols
+    if not kernel_fits(kernel, P.C):
+        pytest.skip("field too large for this kernel")
+    h = qpath.qp_build_qubo(f)
+    R, S = (6, 8) if P.C <= 128 else (4, 5)
+    ref = orc.anneal_structured(P, R, S, seed=9)
+    assert_same(gpu_anneal(h, R, S, 9, kernel=kernel), ref)
+
+
 def test_structured_above_512_cells_falls_back(dev, orc):
     f = inputs.obstacles(24, 24, 0.05, seed=8)
     P = problem(orc, f)
