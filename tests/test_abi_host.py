@@ -67,3 +67,14 @@ def test_threshold_cap_error(L):
     buf = np.zeros(4, np.uint32)
     st = L.qp_thresholds(ct.byref(sc), 0, buf.ctypes.data_as(ct.c_void_p), 4, ct.byref(n))
     assert st == qpath.QP_ERANGE and n.value > 4
+
+
+def test_checked_build_compiles_and_exports_every_declared_symbol():
+    """The checked build (device bounds checks compiled in) builds here and
+    exposes the same ABI; it is run on the GPU by test_gpu_device_checks."""
+    import ctypes as ct
+    path = qbuild.build(checked=True)
+    assert os.path.basename(path) == "libqpath_checked.so"
+    lib = ct.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
