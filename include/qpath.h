@@ -455,7 +455,8 @@ qp_status qp_selftest_wait(int32_t *timed_out, double *waited_ms);
  * array.  *enabled = 1 in the checked build, 0 in the release build (which
  * compiles no checks).  *first_failure = the first failure since the last
  * call, 0 = none; the call clears it.  Sites: 1 threshold table, 2 distance
- * row, 3 spin word, 4 row of S, 5 repair distance, 6 hot-cell list. */
+ * row, 3 spin word, 4 row of S, 5 repair distance, 6 hot-cell list.
+ * QP_ECUDA if the record could not be read from the device. */
 qp_status qp_device_checks(int32_t *enabled, uint32_t *first_failure);
 
 /* Free a handle and its device memory (NULL is ignored). */

@@ -444,11 +444,17 @@ extern "C" qp_status qp_device_checks(int32_t *enabled, uint32_t *first_failure)
   if (!enabled || !first_failure) return fail(QP_EINVAL, "enabled and first_failure are required");
   *enabled = qp::chk::enabled();
   uint32_t w = 0;
+  bool read_failed = false;
   for (uint32_t (*take)() : {qp::chk::rows, qp::chk::kernels, qp::chk::group, qp::chk::repair}) {
     const uint32_t v = take();
+    if (v == 0xFFFFFFFFu) {  // the record could not be read from the device
+      read_failed = true;
+      continue;
+    }
     if (!w) w = v;
   }
   *first_failure = w;
+  if (read_failed) return fail(QP_ECUDA, "could not read the device check record");
   return QP_OK;
 }
 
