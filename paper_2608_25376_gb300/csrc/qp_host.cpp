@@ -287,6 +287,7 @@ extern "C" qp_status qp_build_qubo(const qp_field *f, int32_t A, int32_t B, int3
 
   auto h = std::make_unique<qp_handle>();
   QP_CU(cudaGetDevice(&h->dev));
+  noalloc_preload();
   std::vector<int32_t> cr, cc;
   for (int r = 0; r < f->rows; ++r)
     for (int c = 0; c < f->cols; ++c) {
@@ -722,6 +723,8 @@ bool schedule_lookup(const qp_schedule &sc, DeviceSchedule *out, std::shared_ptr
 }
 
 qp_status set_error(qp_status s, const char *msg) { return fail(s, "%s", msg); }
+
+void clear_error() { g_err.clear(); }
 
 bool device_pointer(const void *p) { return is_device_ptr(p); }
 

@@ -146,7 +146,15 @@ bool handle_struct_view(const qp_handle *h, StructView *out);  // false for a ge
 // false if not cached on this device; *keep (may be NULL) holds the tables alive
 bool schedule_lookup(const qp_schedule &sc, DeviceSchedule *out, std::shared_ptr<const void> *keep);
 qp_status set_error(qp_status s, const char *msg);
+void clear_error();  // empties this thread's qp_last_error message
 bool device_pointer(const void *p);
+
+// Makes the current device load the module that holds qp_anneal_noalloc's
+// fixed scratch array (the driver allocates the array at that moment; CUDA
+// loads modules lazily).  qp_build_qubo calls it, where allocating is
+// allowed, so that the allocation-free entry point never triggers the load.
+// Failure is not reported here: qp_anneal_noalloc reports it on its call.
+void noalloc_preload();
 
 // Every device allocation of the library.  Fault injection for tests: when
 // the environment variable QPATH_FAIL_ALLOC holds N, the next N allocations

@@ -6,47 +6,47 @@
 // buffers, the per-replica working state of large fields); this one uses a
 // fixed scratch array in the library's own device memory instead.
 //
-// The scratch is a file-scope __device__ array of kStaticScratchBytes (16 MiB),
-// so every GPU that loads the library holds it until the process exits.  Host
-// code cannot use the array's name as a device address (it names a host-side
-// stand-in), so the first call on each device looks its address up with
-// cudaGetSymbolAddress, with that device current, and caches it.
-#include <mutex>
-
+// The scratch is a file-scope __device__ array of kStaticScratchBytes (16 MiB).
+// CUDA loads a module lazily, on the first use of one of its kernels or
+// symbols, and the driver allocates the array then; from that moment the
+// device holds it until the process exits.  qp_build_qubo triggers the load
+// (noalloc_preload, with the handle's device current), so a call here, which
+// needs such a handle, finds the array already in place.  Host code cannot
+// use the array's name as a device address (it names a host-side stand-in):
+// every call looks the address up with cudaGetSymbolAddress, with the
+// handle's device current (no cached pointer can outlive a device reset).
 #include "qp_internal.h"
 
 namespace qp {
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(16) << 20;
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) uint32_t g_static_scratch[kStaticScratchBytes / 4];
 
-std::mutex g_scratch_mu;
-uint32_t *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on device `dev` (which must be
-// current); looked up once per device.
-cudaError_t scratch_address(int dev, uint32_t **out) {
-  std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<uint32_t *>(p);
-  }
-  *out = g_scratch_ptr[dev];
+// Device address of the scratch array on the current device.
+cudaError_t scratch_address(uint32_t **out) {
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<uint32_t *>(p);
   return cudaSuccess;
 }
 
 }  // namespace
+
+void noalloc_preload() {
+  uint32_t *p = nullptr;
+  if (scratch_address(&p) != cudaSuccess) cudaGetLastError();
+}
+
 }  // namespace qp
 
 extern "C" qp_status qp_anneal_noalloc(qp_handle *h, int32_t R, const qp_schedule *sc, uint64_t seed,
                                        const uint8_t *init, uint8_t *states_out, int64_t *energies_out,
                                        int64_t *best_out, int32_t replica_offset, void *stream_) {
   using namespace qp;
+  clear_error();
   StructView v;
   if (!h || !handle_struct_view(h, &v)) return set_error(QP_EINVAL, "qp_anneal_noalloc needs a handle built by qp_build_qubo");
   if (!sc || !states_out || !energies_out || R < 1 || replica_offset < 0 ||
@@ -54,7 +54,6 @@ extern "C" qp_status qp_anneal_noalloc(qp_handle *h, int32_t R, const qp_schedul
     return set_error(QP_EINVAL, "qp_anneal_noalloc: bad argument");
   if (sc->n_sweeps < 1 || sc->sweep_begin < 0 || sc->sweep_end < sc->sweep_begin || sc->sweep_end > sc->n_sweeps)
     return set_error(QP_EINVAL, "qp_anneal_noalloc: need 0 <= sweep_begin <= sweep_end <= n_sweeps");
-  if (v.dev < 0 || v.dev >= kMaxDevices) return set_error(QP_EINVAL, "qp_anneal_noalloc: device index out of range");
   int prev = -1;
   if (cudaGetDevice(&prev) != cudaSuccess) return set_error(QP_ECUDA, "qp_anneal_noalloc: cudaGetDevice failed");
   if (prev != v.dev && cudaSetDevice(v.dev) != cudaSuccess)
@@ -81,7 +80,7 @@ extern "C" qp_status qp_anneal_noalloc(qp_handle *h, int32_t R, const qp_schedul
                      "qp_anneal_noalloc: replicas x per-replica state exceed the 16 MiB static scratch "
                      "(R * (ceil(C*C/32) + 1, rounded up to 4) * 4 bytes)");
   uint32_t *scratch = nullptr;
-  const cudaError_t e = scratch_address(v.dev, &scratch);
+  const cudaError_t e = scratch_address(&scratch);
   if (e != cudaSuccess) return set_error(QP_ECUDA, cudaGetErrorString(e));
 
   StructArgs a{};
