@@ -8,15 +8,18 @@ timed region (inputs resident in HBM); the end-to-end figure (`e2e`) rebuilds
 the QUBO from the host field and reads every result back to pinned host memory
 inside the timed region, through the same C ABI a user calls.
 
-Workload (default): 10x10 field, 10% obstacles dropped by a seeded Bernoulli
-draw (90 cells, n = 8100 variables), int32 dE / int64 energies, 1024 replicas
-x 5000 sweeps, geometric T 1e3 -> 1, seed 1.  flip attempts = R * S * (C-1)^2.
+Workload (default, the largest single-GPU configuration): 24x24 field, 15%
+obstacles dropped by a seeded Bernoulli draw (490 cells, n = 240,100
+variables), int16 distances, structured terms only, int32 dE / int64
+energies, 4096 replicas x 10000 sweeps, geometric T 1e3 -> 1, seed 1.
+flip attempts = R * S * (C-1)^2.  The 10x10 workload (92 cells, 1024 x 5000,
+structured and dense) and the others are reported as variants.
 
 `--impl reference` times the CPU oracle (plain C, one thread per replica) on a
 bounded sample of the same workload.
 
 Multi-GPU: replicas shard with no collective on the data path (weak scaling:
-every rank anneals its own 1024 replicas, streams offset by rank); the barrier
+every rank anneals its own replicas, streams offset by rank); the barrier
 and the max-over-ranks time reduction are the only communication.
 """
 from __future__ import annotations
@@ -41,8 +44,9 @@ UNIT = "flip attempts/s"
 # neighbour field of a one-hot state (2 adds), r' and c' (2), 2r'-1 and 2c'-1 (4),
 # the A, A, B products (3), two sums (2), the sign (2), the two comparisons (2)
 OPS_PER_ATTEMPT = 17
-SMS, INT_LANES_PER_SM = 152, 128
+INT_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 512 << 20
+DEFAULT_WORKLOAD = "24x24-p0.15"
 
 
 def parse():
@@ -51,7 +55,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="10x10-p0.10")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-dense", action="store_true")
@@ -94,11 +98,16 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel_tag):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "sweep_rows_10x10.md")
-    if not os.path.exists(p):
+PROFILE_OF = {"24x24-p0.15": "sweep_rows_24x24.md", "10x10-p0.10": "sweep_rows_10x10.md"}
+
+
+def recorded_traffic(workload, kernel_tag="rows"):
+    """DRAM bytes per full launch of the row kernel on `workload`, from the
+    committed ncu summary, if it was taken on the current kernel source (else
+    None)."""
+    name = PROFILE_OF.get(workload)
+    p = os.path.join(ROOT, "profiles", name) if name else None
+    if not p or not os.path.exists(p):
         return None
     txt = open(p).read()
     m = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
@@ -106,6 +115,21 @@ def recorded_traffic(kernel_tag):
     if not m or not t or m.group(1) != kernel_source_hash():
         return None
     return float(t.group(1))
+
+
+def bytes_per_attempt(C):
+    """Algorithmic bytes per flip attempt of the structured sweep (the
+    bytes-per-flip model): each row t of C-1 proposals reads the distance rows
+    of the hot cells of rows t-1 and t+1, 2 rows x C entries x 2 B (int16)."""
+    return 2 * C * 2 / (C - 1)
+
+
+def workload_config(name, f, C, n, w):
+    """The `config` object of both arms' lines (identical for the same workload)."""
+    return {"workload": f"{name} structured", "field": f"{f.rows}x{f.cols}", "cells": C, "variables": n,
+            "replicas": w["replicas"], "sweeps": w["n_sweeps"], "schedule": "geometric 1e3->1",
+            "seed": w["seed"], "attempts_per_step": w["replicas"] * w["n_sweeps"] * (C - 1) ** 2,
+            "l2": "flushed between steps (512 MB write)"}
 
 
 class Clocks:
@@ -161,15 +185,18 @@ def cpu_baseline(w, P, max_seconds=20.0):
     import oracle
     cores = os.cpu_count() or 1
     S = w["n_sweeps"]
-    probe_s = max(1, min(S, 100))
+    probe_s = max(1, min(S, 50))
     t = time.perf_counter()
     oracle.anneal_structured(P, 1, S, seed=w["seed"], sweep_end=probe_s, n_threads=1)
     per_sweep = max((time.perf_counter() - t) / probe_s, 1e-9)
     sweeps = int(max(1, min(S, max_seconds / per_sweep)))
-    t = time.perf_counter()  # one replica through the chosen sweeps sizes the number of waves
-    oracle.anneal_structured(P, [w["replicas"] - 1], S, seed=w["seed"], sweep_end=sweeps, n_threads=1)
-    one = max(time.perf_counter() - t, 1e-9)
-    waves = int(max(1, min(max(1, w["replicas"] // cores), max_seconds / one)))
+    if sweeps < S:
+        waves = 1  # a sweep prefix already fills the budget: one replica per core
+    else:
+        t = time.perf_counter()  # one replica through every sweep sizes the number of waves
+        oracle.anneal_structured(P, [w["replicas"] - 1], S, seed=w["seed"], n_threads=1)
+        one = max(time.perf_counter() - t, 1e-9)
+        waves = int(max(1, min(max(1, w["replicas"] // cores), max_seconds / one)))
     reps = cores * waves
     t = time.perf_counter()
     oracle.anneal_structured(P, reps, S, seed=w["seed"], sweep_end=sweeps, n_threads=cores)
@@ -182,6 +209,9 @@ def cpu_baseline(w, P, max_seconds=20.0):
 
 
 def run_reference(args):
+    """The oracle as it stands, on this host's cores, on the same workload and
+    config as the GPU arm: each step runs `cores` replicas (one thread each)
+    through a sweep prefix sized so the whole run takes a few minutes."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
@@ -192,11 +222,11 @@ def run_reference(args):
     P = oracle.Problem(f.rows, f.cols, f.free_mask, f.start)
     cores = os.cpu_count() or 1
     S = w["n_sweeps"]
-    # bounded step: `cores` replicas through a sweep prefix worth ~ 10 s of CPU
+    step_s = min(10.0, max(1.0, 150.0 / max(1, args.steps)))
     t = time.perf_counter()
-    oracle.anneal_structured(P, 1, S, seed=w["seed"], sweep_end=20, n_threads=1)
-    per_sweep = (time.perf_counter() - t) / 20
-    sweeps = int(max(1, min(S, 10.0 / max(per_sweep, 1e-9))))
+    oracle.anneal_structured(P, 1, S, seed=w["seed"], sweep_end=min(S, 20), n_threads=1)
+    per_sweep = (time.perf_counter() - t) / min(S, 20)
+    sweeps = int(max(1, min(S, step_s / max(per_sweep, 1e-9))))
     for _ in range(args.warmup):
         oracle.anneal_structured(P, cores, S, seed=w["seed"], sweep_end=min(sweeps, 5), n_threads=cores)
     times = []
@@ -207,14 +237,13 @@ def run_reference(args):
     attempts = cores * sweeps * (P.C - 1) ** 2
     ms = 1e3 * statistics.mean(times)
     val = attempts / (ms / 1e3)
+    sample = (f"{cores} of {w['replicas']} replicas (one thread each) x sweeps [0,{sweeps}) of {S} per step, "
+              f"{P.C} cells")
     line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"{args.workload} structured", "cells": P.C, "replicas": cores,
-                       "sweeps": f"[0,{sweeps}) of {S}", "schedule": "geometric 1e3->1",
-                       "parallelism": "replicas over host threads"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{cores} replicas x sweeps [0,{sweeps}) of {S} per step"},
+            "config": workload_config(args.workload, f, P.C, P.n, w),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -408,7 +437,7 @@ def bench_repair(h, states, R, flush, stream):
 
 def cpu_other_rows(P, repair_states, with_pt):
     """The CPU references of the repair and of replica exchange, as they stand,
-    on bounded samples of the same field."""
+    on bounded samples of the 10x10 field (the variants' field)."""
     import oracle
     from oracle import pt_ref, repair_ref
     out = {}
@@ -434,37 +463,91 @@ def cpu_other_rows(P, repair_states, with_pt):
     return out
 
 
-def bench_other_configs(flush, stream):
-    """Throughput on the other workloads of the metric: the 4x4 grid as a dense
-    QUBO (64 replicas x 2000 sweeps) and the 24x24 field with 15% obstacles
-    (structured, int16 d, 4096 replicas x 10000 sweeps), one timed run each."""
+def timed_anneal(h, R, sc, seed, flush, stream, runs=2, warm=True, **kw):
+    """CUDA-event times (ms, on `stream`) of `runs` calls of qp_anneal_ex after
+    an optional warm-up call; L2 flushed before each."""
     import torch
-    from paper_2608_25376_gb300 import inputs, qpath
-    out = {}
-    for name, kernel in (("4x4-dense", qpath.QP_KERNEL_DENSE), ("24x24-p0.15", qpath.QP_KERNEL_AUTO)):
-        w = inputs.WORKLOADS[name]
-        flags = qpath.QP_STRUCTURED | (qpath.QP_DENSE if kernel == qpath.QP_KERNEL_DENSE else 0)
-        h = qpath.qp_build_qubo(w["field"](), flags=flags)
-        n, C = h.info["n"], h.info["C"]
-        R, S = w["replicas"], w["n_sweeps"]
+    from paper_2608_25376_gb300 import qpath
+    n = h.info["n"]
+    st = kw.pop("states", None)
+    if st is None:
         st = torch.zeros((R, n), dtype=torch.uint8, device="cuda")
-        E = torch.zeros(R, dtype=torch.int64, device="cuda")
-        B = torch.zeros(R, dtype=torch.int64, device="cuda")
-        sc = qpath.schedule(S)
-        qpath.qp_anneal_ex(h, R, qpath.schedule(S, sweep_end=2), w["seed"], None, st, E, B, kernel=kernel,
-                           stream=stream)
-        flush.fill_(7)
+    E = torch.zeros(R, dtype=torch.int64, device="cuda")
+    B = torch.zeros(R, dtype=torch.int64, device="cuda")
+    acc = torch.zeros(R, dtype=torch.int64, device="cuda")
+    if warm:
+        qpath.qp_anneal_ex(h, R, sc, seed, None, st, E, B, accepts_out=acc, stream=stream, **kw)
+    ms = []
+    for k in range(runs):
+        flush.fill_(k)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        qpath.qp_anneal_ex(h, R, sc, w["seed"], None, st, E, B, kernel=kernel, stream=stream)
+        qpath.qp_anneal_ex(h, R, sc, seed, None, st, E, B, accepts_out=acc, stream=stream, **kw)
         b.record(stream)
         b.synchronize()
-        ms = a.elapsed_time(b)
-        attempts = R * S * (C - 1) ** 2
-        out[name] = {"value": attempts / (ms / 1e3), "unit": UNIT, "ms": ms, "attempts": attempts,
-                     "kernel": "dense" if kernel == qpath.QP_KERNEL_DENSE else "structured rows",
-                     "best_energy": int(B.min().item())}
-        h.close()
+        ms.append(a.elapsed_time(b))
+    return ms, st, E, B, acc
+
+
+def bench_10x10(flush, stream, pk, pk_kind, skip_settled=True, repair=True):
+    """The 10x10 workload (10% obstacles, 92 cells, 1024 replicas x 5000
+    sweeps): the row kernel (d staged in shared memory), the dense-Q kernel
+    (int16 S, 143 MB, streamed from HBM), the row kernel with settled sweeps
+    skipped (same results) and the repair of the final states.  Returns the
+    variant's record and 8 final states for the CPU repair reference."""
+    import torch
+    from paper_2608_25376_gb300 import inputs, qpath
+    name = "10x10-p0.10"
+    w = inputs.WORKLOADS[name]
+    h = qpath.qp_build_qubo(w["field"](), flags=qpath.QP_STRUCTURED | qpath.QP_DENSE)
+    n, C = h.info["n"], h.info["C"]
+    R, S, seed = w["replicas"], w["n_sweeps"], w["seed"]
+    sc = qpath.schedule(S)
+    attempts = R * S * (C - 1) ** 2
+    out = {"workload": f"{name}: {C} cells, {R} replicas x {S} sweeps", "attempts": attempts}
+    ms, st, E, B, _ = timed_anneal(h, R, sc, seed, flush, stream, runs=3, kernel=qpath.QP_KERNEL_STRUCTURED)
+    rows_ms = statistics.mean(ms)
+    bpa = bytes_per_attempt(C)
+    out["rows"] = {"value": attempts / (rows_ms / 1e3), "unit": UNIT, "kernel_ms": rows_ms,
+                   "bytes_per_flip_GBps": bpa * attempts / (rows_ms / 1e3) / 1e9,
+                   "traffic": recorded_traffic(name)}
+    ref_E, ref_B = E.clone(), B.clone()
+    dms, _, dE, dB, dacc = timed_anneal(h, R, sc, seed, flush, stream, runs=2, kernel=qpath.QP_KERNEL_DENSE)
+    dm = statistics.mean(dms)
+    col_bytes = float(dacc.sum().item()) * ((n + 7) // 8 * 8) * 2  # accepted flips x one int16 row of S
+    out["dense"] = {"value": attempts / (dm / 1e3), "unit": UNIT, "kernel_ms": dm,
+                    "column_bytes_per_launch": col_bytes, "column_GBps": col_bytes / (dm / 1e3) / 1e9,
+                    "frac_of_hbm": col_bytes / (dm / 1e3) / 1e9 / pk["hbm_gbs"] if pk.get("hbm_gbs") else None,
+                    "hbm_peak_GBps": pk.get("hbm_gbs"), "peak_kind": pk_kind,
+                    "same_results_as_rows": bool(torch.equal(dE, ref_E) and torch.equal(dB, ref_B))}
+    if skip_settled:
+        sms, _, sE, sB, _ = timed_anneal(h, R, sc, seed, flush, stream, runs=3, warm=False,
+                                         flags=qpath.QP_ANNEAL_SKIP_SETTLED)
+        out["skip_settled"] = {"ms": statistics.mean(sms), "speedup": rows_ms / statistics.mean(sms),
+                               "same_results": bool(torch.equal(sE, ref_E) and torch.equal(sB, ref_B)),
+                               "note": "sweeps after a replica met no proposal with dE < len are not evaluated; "
+                                       "not a headline number"}
+    sample = None
+    if repair:
+        out["repair"], sample = bench_repair(h, st, R, flush, stream)
+    h.close()
+    return out, sample
+
+
+def bench_4x4_dense(flush, stream):
+    """The 4x4 obstacle-free grid as a dense QUBO (64 replicas x 2000 sweeps)."""
+    from paper_2608_25376_gb300 import inputs, qpath
+    w = inputs.WORKLOADS["4x4-dense"]
+    h = qpath.qp_build_qubo(w["field"](), flags=qpath.QP_STRUCTURED | qpath.QP_DENSE)
+    C = h.info["C"]
+    R, S = w["replicas"], w["n_sweeps"]
+    ms, _, _, B, _ = timed_anneal(h, R, qpath.schedule(S), w["seed"], flush, stream, runs=2,
+                                  kernel=qpath.QP_KERNEL_DENSE)
+    attempts = R * S * (C - 1) ** 2
+    m = statistics.mean(ms)
+    out = {"value": attempts / (m / 1e3), "unit": UNIT, "ms": m, "attempts": attempts, "kernel": "dense",
+           "best_energy": int(B.min().item()), "optimum": 100 * (C - 1)}
+    h.close()
     return out
 
 
@@ -484,19 +567,19 @@ def run_ours(args):
         fcntl.flock(lk, fcntl.LOCK_EX)
         qbuild.build()
         fcntl.flock(lk, fcntl.LOCK_UN)
-    from paper_2608_25376_gb300 import inputs, qpath
+    from paper_2608_25376_gb300 import inputs, qpath, shard
 
     w = inputs.WORKLOADS[args.workload]
     f = w["field"]()
     R, S, seed = w["replicas"], w["n_sweeps"], w["seed"]
-    dense_too = not args.no_dense
-    flags = qpath.QP_STRUCTURED | (qpath.QP_DENSE if dense_too else 0)
-    h = qpath.qp_build_qubo(f, flags=flags)
+    h = qpath.qp_build_qubo(f, flags=qpath.QP_STRUCTURED)
     info = h.info
     C, n = info["C"], info["n"]
     attempts = R * S * (C - 1) ** 2
     sc = qpath.schedule(S)
     dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
     stream = torch.cuda.Stream(device=dev)
     states = torch.zeros((R, n), dtype=torch.uint8, device=dev)
     E = torch.zeros(R, dtype=torch.int64, device=dev)
@@ -505,13 +588,12 @@ def run_ours(args):
     paths = torch.zeros((R, C), dtype=torch.int32, device=dev)
     lens = torch.zeros(R, dtype=torch.int64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-    from paper_2608_25376_gb300 import shard
     offset, _ = shard.replica_range(rank, world, R, "weak")
     rpc = args.replicas_per_cta
     skernel = qpath.QP_KERNEL_STRUCTURED if args.structured_kernel == "rows" else qpath.QP_KERNEL_STRUCTURED_FLAT
 
-    def step(kernel=skernel):
-        qpath.qp_anneal_ex(h, R, sc, seed, None, states, E, best, kernel=kernel, replicas_per_cta=rpc,
+    def step():
+        qpath.qp_anneal_ex(h, R, sc, seed, None, states, E, best, kernel=skernel, replicas_per_cta=rpc,
                            replica_offset=offset, accepts_out=acc, stream=stream)
         qpath.qp_decode_batch(h, R, states, paths, lens, stream=stream)
 
@@ -555,97 +637,57 @@ def run_ours(args):
 
     pk, pk_kind = peaks()
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    peak_tops = SMS * INT_LANES_PER_SM * sm_mhz * 1e6 / 1e12
     ann_ms = statistics.mean(anneal_ms)
+    # the bytes-per-flip roofline: algorithmic bytes per launch / kernel time
+    # against the measured HBM copy rate
+    bpa = bytes_per_attempt(C)
+    achieved_gbs = bpa * attempts / (ann_ms / 1e3) / 1e9
+    # the integer-issue view beside it
+    peak_tops = sms * INT_LANES_PER_SM * sm_mhz * 1e6 / 1e12
     achieved_tops = OPS_PER_ATTEMPT * attempts / (ann_ms / 1e3) / 1e12
-    traffic = recorded_traffic("rows")
-    # the bytes-per-flip view: each row's field is one C-entry d row (int32 in
-    # shared memory for this field) for its C-1 proposals; the threshold table
-    # is read only for proposals inside the table (not counted)
-    bpa = 4.0 * C / (C - 1)
-    achieved_gbs = bpa * attempts / (statistics.mean(anneal_ms) / 1e3) / 1e9
-    smem_gbs = SMS * 128 * sm_mhz * 1e6 / 1e9
-    bytes_view = {"bytes_per_attempt": bpa, "achieved_GBps": achieved_gbs,
-                  "frac_of_shared_memory_bw": achieved_gbs / smem_gbs,
-                  "frac_of_measured_hbm": achieved_gbs / pk["hbm_gbs"] if pk.get("hbm_gbs") else None,
-                  "note": "d rows come from shared memory (staged once per CTA); DRAM traffic per launch is "
-                          "the 'traffic' figure; the sweep is bound by its dependent instruction chain"}
-    roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
-                "frac": achieved_tops / peak_tops, "traffic": traffic, "bytes_per_flip": bytes_view,
+    d_i16 = info["max_d"] <= 32767
+    Cp = (C + 7) // 8 * 8
+    d_where = "shared memory" if C * Cp * 4 <= 160 * 1024 else "L2 (global memory)"
+    roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                "frac": achieved_gbs / pk["hbm_gbs"] if pk.get("hbm_gbs") else None,
+                "traffic": recorded_traffic(args.workload),
                 "kernel": "k_sweep_rows" if args.structured_kernel == "rows" else "k_sweep_structured",
-                "kernel_ms": ann_ms,
-                "note": (f"int32 ops: {OPS_PER_ATTEMPT} algorithmic ops per flip attempt x attempts / kernel time; "
-                         f"peak = {SMS} SMs x {INT_LANES_PER_SM} lanes x {sm_mhz:.0f} MHz ({pk_kind} clock)")}
+                "kernel_ms": ann_ms, "bytes_per_attempt": bpa,
+                "algorithmic_bytes_per_launch": bpa * attempts,
+                "note": (f"bytes-per-flip model: 2 distance rows x {C} int16 entries per row of {C - 1} "
+                         f"proposals ({bpa:.3f} B per attempt); peak = {pk_kind} HBM copy rate; the d rows "
+                         f"come from {d_where}, so DRAM moves only the tables and the states ('traffic')"),
+                "alu_view": {"achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
+                             "frac": achieved_tops / peak_tops,
+                             "note": f"{OPS_PER_ATTEMPT} algorithmic int ops per attempt; peak = {sms} SMs x "
+                                     f"{INT_LANES_PER_SM} lanes x {sm_mhz:.0f} MHz ({pk_kind} clock)"}}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"{args.workload} structured", "field": f"{f.rows}x{f.cols}", "cells": C,
-                       "variables": n, "replicas": R, "sweeps": S, "schedule": "geometric 1e3->1",
-                       "seed": seed, "attempts_per_step": attempts, "l2": "flushed between steps (512 MB write)",
-                       "parallelism": f"replicas x {world} GPU(s), no collective on the data path"},
+            "config": workload_config(args.workload, f, C, n, w),
+            "execution": {"parallelism": f"replicas x {world} GPU(s), no collective on the data path",
+                          "sms": sms, "distances": "int16" if d_i16 else "int32"},
             "roofline": roofline,
             "gpu_launches": 2 * args.steps,
             "clocks": clk,
             "result": {"feasible_replicas": feasible, "best_length": best_len,
                        "accepts_per_attempt": float(acc.sum().item()) / attempts}}
 
-    if dense_too and not args.no_dense and rank == 0:
-        dms = []
-        with torch.cuda.stream(stream):
-            step(qpath.QP_KERNEL_DENSE)
-            for k in range(2):
-                flush.fill_(k)
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                qpath.qp_anneal_ex(h, R, sc, seed, None, states, E, best, kernel=qpath.QP_KERNEL_DENSE,
-                                   replica_offset=offset, accepts_out=acc, stream=stream)
-                b.record(stream)
-                b.synchronize()
-                dms.append(a.elapsed_time(b))
-        dacc = float(acc.sum().item())
-        sbytes = 2  # int16 dense S for this workload
-        col_bytes = dacc * ((n + 7) // 8 * 8) * sbytes
-        dm = statistics.mean(dms)
-        line["variants"] = {"dense": {"value": attempts / (dm / 1e3), "unit": UNIT, "kernel_ms": dm,
-                                      "column_bytes_per_launch": col_bytes,
-                                      "column_GBps": col_bytes / (dm / 1e3) / 1e9,
-                                      "hbm_peak_GBps": pk.get("hbm_gbs"), "peak_kind": pk_kind}}
-
-    if rank == 0 and not args.no_skip_settled:
-        # the same step with settled sweeps skipped (QP_ANNEAL_SKIP_SETTLED):
-        # identical results, less time; not the headline, which evaluates
-        # every proposal
-        ref_E, ref_best = E.clone(), best.clone()
-        sms = []
-        for k in range(3):
-            flush.fill_(k)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            qpath.qp_anneal_ex(h, R, sc, seed, None, states, E, best, replica_offset=offset, stream=stream,
-                               flags=qpath.QP_ANNEAL_SKIP_SETTLED)
-            b.record(stream)
-            b.synchronize()
-            sms.append(a.elapsed_time(b))
-        same = bool(torch.equal(E, ref_E) and torch.equal(best, ref_best))
-        line.setdefault("variants", {})["skip_settled"] = {
-            "ms": statistics.mean(sms), "speedup": ann_ms / statistics.mean(sms),
-            "same_results": same,
-            "note": "same workload and results; sweeps after a replica met no proposal with dE < len are not "
-                    "evaluated"}
+    repair_sample = None
+    if not args.no_dense and rank == 0:
+        line.setdefault("variants", {})["10x10-p0.10"], repair_sample = bench_10x10(
+            flush, stream, pk, pk_kind, skip_settled=not args.no_skip_settled, repair=not args.no_repair)
 
     if not args.no_batch and rank == 0:
         line.setdefault("variants", {})["batched"] = bench_batch(args, flush, stream)
 
-    repair_sample = None
-    if not args.no_repair and rank == 0:
-        line.setdefault("variants", {})["repair"], repair_sample = bench_repair(h, states, R, flush, stream)
-
     if not args.no_other_configs and rank == 0:
-        line.setdefault("variants", {})["other_configs"] = bench_other_configs(flush, stream)
+        line.setdefault("variants", {})["4x4-dense"] = bench_4x4_dense(flush, stream)
 
     if not args.no_replica_exchange and rank == 0:
-        line.setdefault("variants", {})["replica_exchange"] = bench_replica_exchange(f, flush, stream)
+        line.setdefault("variants", {})["replica_exchange"] = bench_replica_exchange(
+            inputs.WORKLOADS["10x10-p0.10"]["field"](), flush, stream)
 
     if not args.no_warm_start and rank == 0:
         line["warm_start"] = bench_warm_start()
@@ -661,7 +703,7 @@ def run_ours(args):
         pin_lens = torch.empty(R, dtype=torch.int64, pin_memory=True)
         mask = np.ascontiguousarray(f.free_mask, np.uint8)
         e_times = []
-        n_e2e = max(1, min(args.steps, 3))
+        n_e2e = max(1, min(args.steps, 2))
         for k in range(n_e2e):
             flush.fill_(k)
             torch.cuda.synchronize()
@@ -674,19 +716,21 @@ def run_ours(args):
             torch.cuda.synchronize()
             e_times.append(time.perf_counter() - t0)
             h2.close()
-        Cp = (C + 7) // 8 * 8
-        h2d = mask.nbytes + C * Cp * 2 + C * C * 4 + R * n  # field, d (int16 + int32), states for decode
-        d2h = R * n + 16 * R + R * C * 4 + 8 * R
+        d_bytes = C * Cp * (2 if d_i16 else 4)
+        h2d = mask.nbytes + d_bytes + R * n  # field, d, the host states staged again for the decode
+        d2h = R * n + 16 * R + R * C * 4 + 8 * R  # states, energies + best, paths, lengths
         em = statistics.mean(e_times)
         line["e2e"] = {"value": world * attempts / em, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h, "ms_per_step": em * 1e3,
+                       "d2h_bytes_per_step": d2h, "ms_per_step": em * 1e3, "steps": n_e2e,
                        "api": "qp_build_qubo + qp_anneal_ex + qp_decode_batch on pinned host buffers"}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         P = oracle.Problem(f.rows, f.cols, f.free_mask, f.start)
         line["cpu_baseline"] = cpu_baseline(w, P)
-        line["cpu_baseline"]["other_rows"] = cpu_other_rows(P, repair_sample, not args.no_replica_exchange)
+        f10 = inputs.WORKLOADS["10x10-p0.10"]["field"]()
+        P10 = oracle.Problem(f10.rows, f10.cols, f10.free_mask, f10.start)
+        line["cpu_baseline"]["other_rows"] = cpu_other_rows(P10, repair_sample, not args.no_replica_exchange)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
