@@ -197,19 +197,22 @@ qp_status qp_anneal_ex(qp_handle *h, int32_t replicas, const qp_schedule *sched,
  * or a loop that cannot afford an allocation's latency.  The paper has no
  * counterpart; this is a deployment entry point.
  * The per-replica working state lives in a fixed 16 MiB array in the library's
- * own device memory (held by every GPU that loads the library until exit):
- * R * (ceil(C*C/32) + 1, rounded up to 4) * 4 bytes must fit, else QP_ERANGE.
+ * own device memory: R * (ceil(C*C/32) + 1, rounded up to 4) * 4 bytes must
+ * fit, else QP_ERANGE.  CUDA loads the array's module lazily and allocates the
+ * array then; qp_build_qubo does that for the handle's device (it is the
+ * call that allocates), so this call needs a handle built by qp_build_qubo
+ * and, from then on, the device holds the 16 MiB until the process exits.
  * Every buffer (init_states, states_out, energies_out, best_out) must be
  * device memory (QP_EINVAL otherwise); init_states and best_out may be NULL.
  * The schedule's threshold tables must already exist on the device: one
  * earlier qp_anneal/qp_anneal_ex call with the same n_sweeps, T0 and T1 builds
  * them, and they stay cached unless more than 4 GiB of other schedules' tables
- * were built since (QP_EINVAL otherwise).  The first call on each device looks up the
- * array's device address; make that first call before any stream capture.
- * Every call shares the one array, and each kernel rewrites the part it uses
- * before reading it, so nothing carries over between calls; calls that overlap
- * on the GPU (other streams, other threads) race on it and must be
- * serialised by the caller.  Asynchronous on cuda_stream. */
+ * were built since (QP_EINVAL otherwise).  Each call looks up the array's
+ * device address afresh (cudaGetSymbolAddress), so nothing stale survives a
+ * device reset.  Every call shares the one array, and each kernel rewrites
+ * the part it uses before reading it, so nothing carries over between calls;
+ * calls that overlap on the GPU (other streams, other threads) race on it and
+ * must be serialised by the caller.  Asynchronous on cuda_stream. */
 qp_status qp_anneal_noalloc(qp_handle *h, int32_t replicas, const qp_schedule *sched, uint64_t seed,
                             const uint8_t *init_states, uint8_t *states_out, int64_t *energies_out,
                             int64_t *best_out, int32_t replica_offset, void *cuda_stream);
@@ -409,10 +412,38 @@ qp_status qp_ws_set_forward_mode(qp_ws *ws, int32_t mode);
 qp_status qp_ws_grads(qp_ws *ws, const float *feats, const int32_t *labels, const int32_t *steps, int32_t M,
                       float *grads_out, float *loss_out, void *cuda_stream);
 
-/* One training step: gradients as in qp_ws_grads, then Adam (beta1 0.9,
- * beta2 0.999, eps 1e-8) with learning rate lr. */
+/* One training step: gradients as in qp_ws_grads, then Adam (Kingma & Ba,
+ * ICLR 2015: bias-corrected first and second moments; beta1 0.9f, beta2
+ * 0.999f, eps 1e-8f as fp32 constants, step count from 1) with learning rate
+ * lr, in fp32 on the master weights; the bf16 weights and their transposes are
+ * rewritten from the updated masters (round to nearest even). */
 qp_status qp_ws_train_step(qp_ws *ws, const float *feats, const int32_t *labels, const int32_t *steps, int32_t M,
                            float lr, float *loss_out, void *cuda_stream);
+
+/* Read-back of the model for checking it (no counterpart in the paper).
+ * qp_ws_get_state: one fp32 tensor set in the flat get/set layout -- the
+ * master parameters (QP_WS_STATE_PARAMS), Adam's first and second moments
+ * (QP_WS_STATE_ADAM_M, _ADAM_V; zero before the first step) or the gradients
+ * of the last qp_ws_grads / qp_ws_train_step call (QP_WS_STATE_GRADS: the
+ * very gradients its Adam step applied).  out: param_count floats (host).
+ * qp_ws_get_buffer: raw contents of a device buffer, rows 0..rows-1 of the
+ * last forward / backward pass (bf16 as uint16 bits, row-major, 16 columns
+ * for QP_WS_BUF_X0, 256 otherwise; QP_WS_BUF_Z is fp32): the input features
+ * X0, the hidden activations H1..H3 (written by passes that keep them:
+ * qp_ws_grads, qp_ws_train_step, or any pass in the layered mode), the logits
+ * Z, their gradient dZ and the back-propagated dH1..dH3 (the gradients at
+ * H1..H3 after the ReLU mask).  QP_WS_BUF_W_BF16 + l and QP_WS_BUF_WT_BF16 +
+ * l (l = 0..3) give layer l's bf16 weight [out x in] and its transpose
+ * [in x out] (rows ignored).  QP_EINVAL for an unknown buffer or rows beyond
+ * the buffers' capacity (the largest M so far, rounded up to 128); rows past
+ * the last pass's M hold no defined values.  Both wait for the device. */
+enum { QP_WS_STATE_PARAMS = 0, QP_WS_STATE_ADAM_M = 1, QP_WS_STATE_ADAM_V = 2, QP_WS_STATE_GRADS = 3 };
+qp_status qp_ws_get_state(qp_ws *ws, int32_t which, float *out);
+enum {
+  QP_WS_BUF_X0 = 0, QP_WS_BUF_H1 = 1, QP_WS_BUF_H2 = 2, QP_WS_BUF_H3 = 3, QP_WS_BUF_Z = 4, QP_WS_BUF_DZ = 5,
+  QP_WS_BUF_DH1 = 6, QP_WS_BUF_DH2 = 7, QP_WS_BUF_DH3 = 8, QP_WS_BUF_W_BF16 = 16, QP_WS_BUF_WT_BF16 = 32
+};
+qp_status qp_ws_get_buffer(qp_ws *ws, int32_t which, int32_t rows, void *out);
 
 /* Logits of one field's C cells (row stride ld >= C, host) -> a feasible
  * one-hot state (C*C bytes, t-major) and its path: the start cell takes step
@@ -438,6 +469,28 @@ qp_status qp_ws_decode_walk(const float *logits, int32_t ld, int32_t C, int32_t 
  * int32 (host; either may be NULL).  QP_ERANGE above 256 cells. */
 qp_status qp_ws_infer(qp_ws *ws, const qp_field *field, const int32_t *d, uint8_t *state_out, int32_t *path_out,
                       void *cuda_stream);
+
+/* Device decode of the warm start (no counterpart in the paper).
+ * qp_ws_expected_steps: E_m = sum_{t < T_m} t softmax(logits_m)_t over the
+ * first T_m = steps[m] logits of row m (T_m clamped to [1, min(256, ld)]), in
+ * fp32, for M rows of row stride ld.  logits (M*ld fp32), steps (M int32) and
+ * E_out (M fp32) are device buffers (QP_EINVAL otherwise).  Asynchronous.
+ * qp_ws_walk: a feasible one-hot seed of the handle's field by a walk: step 0
+ * is the start cell; each later step goes to a cell not yet visited, chosen
+ * among the unvisited cells within `slack` (same units as d, >= 0) of the
+ * nearest unvisited distance from the current cell, as the smallest (score,
+ * distance, cell id) when score (C fp32, finite, -0 counts as +0) is given,
+ * else the smallest (distance, cell id).  slack = 0 with score = the expected
+ * steps is qp_ws_decode_walk; no score is the plain nearest-cell walk.
+ * Outputs (device, each may be NULL, not both state and path): state_out C*C
+ * bytes (zeroed, then one 1 per step), path_out C int32, length_out one int64
+ * (the path's length in d units).  Needs a handle from qp_build_qubo (QP_EINVAL
+ * otherwise); QP_ERANGE for more than 4096 cells or max d >= 2^20; host
+ * buffers are refused (QP_EINVAL).  One warp runs the field; asynchronous. */
+qp_status qp_ws_expected_steps(const float *logits, int32_t ld, int32_t M, const int32_t *steps, float *E_out,
+                               void *cuda_stream);
+qp_status qp_ws_walk(qp_handle *h, const float *score, int32_t slack, uint8_t *state_out, int32_t *path_out,
+                     int64_t *length_out, void *cuda_stream);
 
 /* Self-test of the bounded wait that guards the library's asynchronous copies
  * (no counterpart in the paper): one warp waits on an mbarrier phase that

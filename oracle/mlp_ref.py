@@ -8,7 +8,10 @@ weights, hidden activations, the back-propagated gradients dZ and dH) is
 rounded to bfloat16 (round half to even) at the same places, so the GPU can be
 compared within accumulation-order differences; with ``bf16=False`` it is the
 exact float64 network used to pin the backward pass by finite differences.
-Also: the greedy decode of step logits into a path.
+Also: one layer at a time (forward, the cross-entropy gradient, backward) on
+explicit inputs, so each GPU product can be checked on the GPU's own stored
+operands; the Adam update (Kingma & Ba, ICLR 2015, Algorithm 1); and the
+decodes of step logits into a path.
 """
 from __future__ import annotations
 
@@ -88,6 +91,58 @@ def loss_and_grads(params, feats, labels, steps, bf16_storage=True):
     return loss, flatten(grads)
 
 
+def layer_forward(X, Wq, b, relu):
+    """One layer on given operands, summed in float64: A = X Wq^T + b, then
+    ReLU when relu (no rounding: the caller rounds what is stored)."""
+    A = np.asarray(X, np.float64) @ np.asarray(Wq, np.float64).T + np.asarray(b, np.float64)
+    return np.maximum(A, 0.0) if relu else A
+
+
+def ce_grad(Z, labels, steps, M):
+    """Gradient of the mean softmax cross-entropy with respect to the logits Z
+    (rows with label < 0 contribute nothing; logits t >= steps are masked; M is
+    the divisor of the mean), in float64."""
+    Z = np.asarray(Z, np.float64)
+    T = Z.shape[1]
+    mask = np.arange(T)[None, :] < np.asarray(steps)[:, None]
+    valid = np.asarray(labels) >= 0
+    Zm = np.where(mask, Z, -np.inf)
+    Zm = Zm - Zm.max(axis=1, keepdims=True)
+    P = np.where(mask, np.exp(Zm), 0.0)
+    P /= P.sum(axis=1, keepdims=True)
+    lab = np.where(valid, labels, 0)
+    Y = np.zeros_like(P)
+    Y[np.arange(len(lab)), lab] = 1.0
+    return np.where(valid[:, None], (P - Y) / M, 0.0)
+
+
+def layer_backward(dY, X, Wq, relu_ref):
+    """Back-propagation through one layer on given operands, float64:
+    dW = dY^T X, db = column sums of dY, and (when relu_ref is given) the
+    gradient at the layer's input, dY Wq, zeroed where relu_ref <= 0."""
+    dY = np.asarray(dY, np.float64)
+    dW = dY.T @ np.asarray(X, np.float64)
+    db = dY.sum(axis=0)
+    dX = None
+    if relu_ref is not None:
+        dX = np.where(np.asarray(relu_ref) > 0, dY @ np.asarray(Wq, np.float64), 0.0)
+    return dW, db, dX
+
+
+def adam_step(w, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba, "Adam: A Method for Stochastic
+    Optimization", ICLR 2015, Algorithm 1) in float64, t counting from 1:
+        m_t = b1 m_{t-1} + (1 - b1) g,   v_t = b2 v_{t-1} + (1 - b2) g^2,
+        w_t = w_{t-1} - lr (m_t / (1 - b1^t)) / (sqrt(v_t / (1 - b2^t)) + eps).
+    -> (w_t, m_t, v_t)"""
+    w, m, v, g = (np.asarray(a, np.float64) for a in (w, m, v, g))
+    m_t = b1 * m + (1.0 - b1) * g
+    v_t = b2 * v + (1.0 - b2) * g * g
+    m_hat = m_t / (1.0 - b1 ** t)
+    v_hat = v_t / (1.0 - b2 ** t)
+    return w - lr * m_hat / (np.sqrt(v_hat) + eps), m_t, v_t
+
+
 def greedy_decode(logits, C, start_cell):
     """Step 0 is the start cell; then the largest logit over unassigned cells
     and free steps 1..C-1 fixes one (cell, step) pair at a time; ties go to the
@@ -124,6 +179,38 @@ def walk_decode(logits, C, start_cell, d):
     for _ in range(1, C):
         cands = [j for j in range(C) if j not in seen]
         nxt = min(cands, key=lambda j: (int(d[cur][j]), e[j], j))
+        path.append(nxt)
+        seen.add(nxt)
+        cur = nxt
+    return path
+
+
+def expected_steps(logits, steps):
+    """E_m = sum_{t < T_m} t softmax(z_m)_t over the first T_m = steps[m]
+    logits of each row, in float64."""
+    Z = np.asarray(logits, np.float64)
+    out = np.empty(len(Z))
+    for m, T in enumerate(np.asarray(steps)):
+        z = Z[m, :T] - Z[m, :T].max()
+        p = np.exp(z)
+        out[m] = float((p * np.arange(T)).sum() / p.sum())
+    return out
+
+
+def walk(d, C, start_cell, score=None, slack=0):
+    """The walk decode, step by step: from the start cell, each step goes to an
+    unvisited cell j with d(cur, j) <= (nearest unvisited distance) + slack,
+    choosing the smallest (score[j], d(cur, j), j), or the smallest
+    (d(cur, j), j) without a score.  Scores compare as real numbers."""
+    path, seen, cur = [start_cell], {start_cell}, start_cell
+    for _ in range(1, C):
+        cands = [j for j in range(C) if j not in seen]
+        dmin = min(int(d[cur][j]) for j in cands)
+        near = [j for j in cands if int(d[cur][j]) <= dmin + slack]
+        if score is None:
+            nxt = min(near, key=lambda j: (int(d[cur][j]), j))
+        else:
+            nxt = min(near, key=lambda j: (float(score[j]), int(d[cur][j]), j))
         path.append(nxt)
         seen.add(nxt)
         cur = nxt

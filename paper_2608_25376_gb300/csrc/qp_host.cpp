@@ -706,6 +706,8 @@ bool handle_struct_view(const qp_handle *h, StructView *out) {
   out->B = h->B;
   out->d = h->d_dev.p;
   out->d_i16 = h->d_i16;
+  out->max_d = h->max_d;
+  out->d32 = h->d32_dev.as<int32_t>();
   return true;
 }
 

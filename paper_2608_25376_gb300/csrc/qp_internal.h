@@ -138,9 +138,10 @@ cudaError_t launch_pt_exchange(const PtArgs &a, cudaStream_t st);
 
 struct StructView {
   int dev;
-  int32_t C, Cp, start, A, B;
+  int32_t C, Cp, start, A, B, max_d;
   const void *d;
   bool d_i16;
+  const int32_t *d32;  // C x C int32 on the device
 };
 bool handle_struct_view(const qp_handle *h, StructView *out);  // false for a generic QUBO
 // false if not cached on this device; *keep (may be NULL) holds the tables alive

@@ -76,6 +76,17 @@ __device__ __forceinline__ int scan_row_field(const uint32_t *row, int Cw, const
   return cnt;
 }
 
+// F_u, the field of row u: the d row of its single hot cell (the per-row cache
+// hot1) or, when the row does not hold exactly one cell, a scan of its bits.
+// F must be zero on entry.
+template <typename DT, int NCH, int DMODE>
+__device__ __forceinline__ void row_field(const uint32_t *st, int Cw, const int16_t *hot1, int u, const void *d,
+                                          int Cp, int C, int lane, int (&F)[NCH][4]) {
+  const int h = hot1[u];
+  if (h >= 0) add_drow<DT, NCH, DMODE>(d, Cp, C, h, lane, 1, F);
+  else { int one; scan_row_field<DT, NCH, DMODE>(st + u * Cw, Cw, d, Cp, C, lane, F, &one); }
+}
+
 // The single hot cell of a row, or -1 if the row does not hold exactly one.
 __device__ __forceinline__ int row_single(const uint32_t *row, int Cw, int lane) {
   const uint32_t word = lane < Cw ? row[lane] : 0u;
@@ -281,9 +292,11 @@ __device__ __forceinline__ void rows_init(const StructArgs &a, int r, uint32_t *
       }
   E_out = (long long)B * warp_sum64(hd) + (long long)A * (pen_rows + warp_sum64(pen_cols));
   viol_out = viol + __reduce_add_sync(kFull, viol_cols);
+  // columns outside the field get 2A (as if visited once): the row kernel's
+  // whole-row pre-test then never passes on them in a one-hot row
 #pragma unroll
   for (int c = 0; c < NCH; ++c)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) tAc[c][j] = twoA * cs[c][j];
+    for (int j = 0; j < 4; ++j) tAc[c][j] = 128 * c + 4 * lane + j < C ? twoA * cs[c][j] : twoA;
 
 }

@@ -48,9 +48,10 @@ using namespace dev;
 // batched persistent launch.  st: the replica's C x Cw row bitsets; hot1: its
 // per-row single-cell cache (C entries); d: the distance matrix (global or
 // shared memory, per DMODE).
-template <typename DT, int NCH, int DMODE>
+template <typename DT, int NCH, int DMODE, int LA>
 __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_t *st, int16_t *hot1,
                                              const void *d, int lane) {
+  static_assert(LA == 1 || LA == 2, "field look-ahead of 1 or 2 rows");
   const int C = a.C, Cp = a.Cp, s0 = a.start, A = a.A, B = a.B;
   const int twoA = 2 * A;
   const int Cw = (C + 31) >> 5;
@@ -85,25 +86,21 @@ __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_
     // draw of a proposal with dE >= dq is rejected by two compares
     const int dq = len > 1 ? min(len - 1, max(1, (int)fminf(8.0f / cT, 1.0e9f))) : 1;
     const uint32_t Q = len > 1 ? __ldg(a.thr + a.thr_off[ts] + dq) : 0u;
-    int P[NCH][4], Cu[NCH][4], N[NCH][4], Nn[NCH][4];
+    // P, Cu, N: the fields of rows t-1, t, t+1; N1 (and N2 when LA = 2): rows
+    // t+2 (and t+3).  Row t+1+LA's field is loaded LA rows ahead of its use, so
+    // an L2 read of d (LA = 2 when d is in global memory) has that many rows of
+    // work to hide behind.
+    int P[NCH][4], Cu[NCH][4], N[NCH][4], N1[NCH][4], N2[NCH][4];
+    int(&NL)[NCH][4] = LA == 2 ? N2 : N1;  // the field being loaded
     zero<NCH>(P);
     zero<NCH>(Cu);
-    zero<NCH>(Nn);
+    zero<NCH>(N1);
+    zero<NCH>(N2);
     add_drow<DT, NCH, DMODE>(d, Cp, C, s0, lane, 1, P);  // row 0 holds only the start cell
-    {
-      const int h = hot1[1];
-      if (h >= 0) add_drow<DT, NCH, DMODE>(d, Cp, C, h, lane, 1, Cu);
-      else { int one; scan_row_field<DT, NCH, DMODE>(st + Cw, Cw, d, Cp, C, lane, Cu, &one); }
-    }
-    // Row t needs F_{t+1} and its own bits; both are loaded one row ahead
-    // (neither can change before row t is processed), and the single-cell
-    // cache two rows ahead.
-    if (C > 2) {
-      const int h = hot1[2];
-      if (h >= 0) add_drow<DT, NCH, DMODE>(d, Cp, C, h, lane, 1, Nn);
-      else { int one; scan_row_field<DT, NCH, DMODE>(st + 2 * Cw, Cw, d, Cp, C, lane, Nn, &one); }
-    }
-    int h2 = C > 3 ? hot1[3] : -1;
+    row_field<DT, NCH, DMODE>(st, Cw, hot1, 1, d, Cp, C, lane, Cu);
+    if (C > 2) row_field<DT, NCH, DMODE>(st, Cw, hot1, 2, d, Cp, C, lane, N1);
+    if (LA == 2 && C > 3) row_field<DT, NCH, DMODE>(st, Cw, hot1, 3, d, Cp, C, lane, N2);
+    int hl = C > 2 + LA ? hot1[2 + LA] : -1;  // the single cell of row t+1+LA
     int xnn[NCH];
 #pragma unroll
     for (int c = 0; c < NCH; ++c)
@@ -117,15 +114,22 @@ __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_
         xn[c] = xnn[c];
         rt += __popc(xn[c]);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) N[c][j] = Nn[c][j];
+        for (int j = 0; j < 4; ++j) {
+          N[c][j] = N1[c][j];
+          if (LA == 2) N1[c][j] = N2[c][j];
+        }
       }
-      if (t + 2 < C && h2 >= 0) {
-        set_drow<DT, NCH, DMODE>(d, Cp, C, h2, lane, Nn);
+      // F_{t+1+LA}: the d row of that row's single hot cell, else a scan of its bits
+      if (t + 1 + LA < C && hl >= 0) {
+        set_drow<DT, NCH, DMODE>(d, Cp, C, hl, lane, NL);
       } else {
-        zero<NCH>(Nn);
-        if (t + 2 < C) { int one; scan_row_field<DT, NCH, DMODE>(row + 2 * Cw, Cw, d, Cp, C, lane, Nn, &one); }
+        zero<NCH>(NL);
+        if (t + 1 + LA < C) {
+          int one;
+          scan_row_field<DT, NCH, DMODE>(row + (1 + LA) * Cw, Cw, d, Cp, C, lane, NL, &one);
+        }
       }
-      h2 = t + 3 < C ? hot1[t + 3] : -1;
+      hl = t + 2 + LA < C ? hot1[t + 2 + LA] : -1;
 #pragma unroll
       for (int c = 0; c < NCH; ++c)
         xnn[c] = (t + 1 < C && 128 * c + 4 * lane < C)
@@ -134,27 +138,48 @@ __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_
       const int rt0 = rt;
       bool flipped = false;
       const int tC = t * C;
+      // The whole row first, as one test: with base = B f + 2A c_i, a proposal
+      // can matter (dE < len) only if base < len - 2A(r-1) (x = 0) or
+      // base > 2A(3-r) - len (x = 1).  Both bounds for every column give a
+      // superset of the proposals that matter (columns outside the field carry
+      // base = 2A, inside both bounds when r = 1 and len < 2A); when none
+      // passes, no proposal of the row can flip or needs a draw.
+      bool maybe = false;
+      {
+        const int lo = len - twoA * (rt - 1), hi = twoA * (3 - rt) - len;
 #pragma unroll
-      for (int c = 0; c < NCH; ++c) {
-        if (128 * c >= C) break;
-        // base = B f + 2A c_i;  dE = base + 2A(r-1) (x = 0),  2A(3-r) - base (x = 1)
-        int base[4], de[4];
-        unsigned hit = 0;
-        {
-          const int k0 = twoA * (rt - 1), k1 = twoA * (3 - rt);
+        for (int c = 0; c < NCH; ++c) {
+          if (128 * c >= C) break;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            base[j] = B * (P[c][j] + N[c][j]) + tAc[c][j];
-            de[j] = ((xn[c] >> j) & 1) ? k1 - base[j] : base[j] + k0;
-            // the proposal matters iff dE <= 0 (accepted) or 1 <= dE < len (a draw decides): dE < len
-            hit |= (unsigned)(de[j] < len) << j;
+            const int b = B * (P[c][j] + N[c][j]) + tAc[c][j];
+            maybe |= (b < lo) | (b > hi);
           }
         }
-        if (__any_sync(kFull, hit & validc[c])) {
-          any_hit = true;
-          flipped |= row_chunk<DT, NCH, DMODE>(c, t, s, tC, base, de, xn[c], validc[c], tAc[c], rt, Cu, row, E, acc,
-                                               viol, d, Cp, C, lane, twoA, len, lenm1, cT, dq, Q, thr, rg,
-                                               a.key0, a.key1);
+      }
+      if (__any_sync(kFull, maybe)) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+          if (128 * c >= C) break;
+          // base = B f + 2A c_i;  dE = base + 2A(r-1) (x = 0),  2A(3-r) - base (x = 1)
+          int base[4], de[4];
+          unsigned hit = 0;
+          {
+            const int k0 = twoA * (rt - 1), k1 = twoA * (3 - rt);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              base[j] = B * (P[c][j] + N[c][j]) + tAc[c][j];
+              de[j] = ((xn[c] >> j) & 1) ? k1 - base[j] : base[j] + k0;
+              // the proposal matters iff dE <= 0 (accepted) or 1 <= dE < len (a draw decides): dE < len
+              hit |= (unsigned)(de[j] < len) << j;
+            }
+          }
+          if (__any_sync(kFull, hit & validc[c])) {
+            any_hit = true;
+            flipped |= row_chunk<DT, NCH, DMODE>(c, t, s, tC, base, de, xn[c], validc[c], tAc[c], rt, Cu, row, E,
+                                                 acc, viol, d, Cp, C, lane, twoA, len, lenm1, cT, dq, Q, thr, rg,
+                                                 a.key0, a.key1);
+          }
         }
       }
       viol += (rt != 1) - (rt0 != 1);
@@ -222,7 +247,7 @@ __global__ void __launch_bounds__(rows_max_warps<NCH>() * 32) k_sweep_rows(const
   __syncthreads();
   const int r = blockIdx.x * W + warp;
   if (r >= a.R) return;  // no CTA-wide barrier after this point
-  rows_replica<DT, NCH, DMODE>(a, r, st, hot1, d, lane);
+  rows_replica<DT, NCH, DMODE, DMODE == 0 ? 2 : 1>(a, r, st, hot1, d, lane);
 }
 
 // Batched persistent sweep: many fields of uneven size in one launch.  Each
@@ -247,7 +272,7 @@ __global__ void __launch_bounds__(rows_max_warps<NCH>() * 32)
     if (u >= n_units) break;
     const int2 unit = units[u];
     const StructArgs a = fields[unit.x];
-    rows_replica<int16_t, NCH, 0>(a, unit.y, st, hot1, a.d, lane);
+    rows_replica<int16_t, NCH, 0, 1>(a, unit.y, st, hot1, a.d, lane);
     __syncwarp();
   }
 }

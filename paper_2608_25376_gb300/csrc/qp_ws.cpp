@@ -407,6 +407,60 @@ extern "C" qp_status qp_ws_train_step(qp_ws *m, const float *feats, const int32_
   return QP_OK;
 }
 
+// ----------------------------------------------------------------------------- read-back
+extern "C" qp_status qp_ws_get_state(qp_ws *m, int32_t which, float *out) {
+  if (!m || !out || which < QP_WS_STATE_PARAMS || which > QP_WS_STATE_GRADS)
+    return set_error(QP_EINVAL, "bad argument");
+  DevGuard g(m->dev);
+  WS_CU(cudaDeviceSynchronize());
+  size_t o = 0;
+  for (int l = 0; l < kLayers; ++l) {
+    const Buf &W = which == QP_WS_STATE_PARAMS ? m->w[l]
+                   : which == QP_WS_STATE_ADAM_M ? m->mw[l]
+                   : which == QP_WS_STATE_ADAM_V ? m->vw[l] : m->gw[l];
+    const Buf &B = which == QP_WS_STATE_PARAMS ? m->b[l]
+                   : which == QP_WS_STATE_ADAM_M ? m->mb[l]
+                   : which == QP_WS_STATE_ADAM_V ? m->vb[l] : m->gb[l];
+    const size_t nw = (size_t)kDimOut[l] * kDimIn[l];
+    WS_CU(cudaMemcpy(out + o, W.p, nw * 4, cudaMemcpyDeviceToHost));
+    o += nw;
+    WS_CU(cudaMemcpy(out + o, B.p, (size_t)kDimOut[l] * 4, cudaMemcpyDeviceToHost));
+    o += kDimOut[l];
+  }
+  return QP_OK;
+}
+
+extern "C" qp_status qp_ws_get_buffer(qp_ws *m, int32_t which, int32_t rows, void *out) {
+  if (!m || !out) return set_error(QP_EINVAL, "bad argument");
+  DevGuard g(m->dev);
+  if (which >= QP_WS_BUF_W_BF16 && which < QP_WS_BUF_W_BF16 + kLayers) {
+    const int l = which - QP_WS_BUF_W_BF16;
+    WS_CU(cudaDeviceSynchronize());
+    WS_CU(cudaMemcpy(out, m->wb[l].p, (size_t)kDimOut[l] * kDimIn[l] * 2, cudaMemcpyDeviceToHost));
+    return QP_OK;
+  }
+  if (which >= QP_WS_BUF_WT_BF16 && which < QP_WS_BUF_WT_BF16 + kLayers) {
+    const int l = which - QP_WS_BUF_WT_BF16;
+    WS_CU(cudaDeviceSynchronize());
+    WS_CU(cudaMemcpy(out, m->wt[l].p, (size_t)kDimOut[l] * kDimIn[l] * 2, cudaMemcpyDeviceToHost));
+    return QP_OK;
+  }
+  if (rows < 1 || rows > m->cap) return set_error(QP_EINVAL, "rows beyond the last pass's buffers");
+  const Buf *b = nullptr;
+  size_t row_bytes = (size_t)kHid * 2;
+  switch (which) {
+    case QP_WS_BUF_X0: b = &m->x0; row_bytes = (size_t)kIn * 2; break;
+    case QP_WS_BUF_H1: case QP_WS_BUF_H2: case QP_WS_BUF_H3: b = &m->h[which - QP_WS_BUF_H1]; break;
+    case QP_WS_BUF_Z: b = &m->z; row_bytes = (size_t)kOut * 4; break;
+    case QP_WS_BUF_DZ: b = &m->dz; row_bytes = (size_t)kOut * 2; break;
+    case QP_WS_BUF_DH1: case QP_WS_BUF_DH2: case QP_WS_BUF_DH3: b = &m->dh[which - QP_WS_BUF_DH1]; break;
+    default: return set_error(QP_EINVAL, "unknown buffer");
+  }
+  WS_CU(cudaDeviceSynchronize());
+  WS_CU(cudaMemcpy(out, b->p, (size_t)rows * row_bytes, cudaMemcpyDeviceToHost));
+  return QP_OK;
+}
+
 // ----------------------------------------------------------------------------- features
 extern "C" qp_status qp_ws_features(const qp_field *f, float *feats_out, int32_t *n_cells) {
   if (!f || f->rows < 1 || f->cols < 1) return set_error(QP_EINVAL, "bad field");

@@ -31,6 +31,7 @@ SYMBOLS = ["qp_build_qubo", "qp_build_from_dense", "qp_qubo_info", "qp_export_de
            "qp_batch_run", "qp_batch_info", "qp_batch_destroy", "qp_anneal_batch", "qp_decode_path",
            "qp_decode_batch", "qp_repair_batch", "qp_repair_path", "qp_anneal_timed", "qp_anneal_pt", "qp_ws_create", "qp_ws_destroy", "qp_ws_param_count", "qp_ws_get_params",
            "qp_ws_set_params", "qp_ws_features", "qp_ws_forward", "qp_ws_set_forward_mode", "qp_ws_grads", "qp_ws_train_step",
+           "qp_ws_get_state", "qp_ws_get_buffer", "qp_ws_expected_steps", "qp_ws_walk",
            "qp_ws_decode", "qp_ws_decode_walk", "qp_ws_infer", "qp_selftest_wait", "qp_device_checks", "qp_destroy",
            "qp_last_error"]
 
@@ -113,6 +114,10 @@ def lib():
                 "qp_ws_set_forward_mode": [vp, i32],
                 "qp_ws_grads": [vp, vp, vp, vp, i32, vp, vp, vp],
                 "qp_ws_train_step": [vp, vp, vp, vp, i32, ct.c_float, vp, vp],
+                "qp_ws_get_state": [vp, i32, vp],
+                "qp_ws_expected_steps": [vp, i32, i32, vp, vp, vp],
+                "qp_ws_walk": [vp, vp, i32, vp, vp, vp, vp],
+                "qp_ws_get_buffer": [vp, i32, i32, vp],
                 "qp_ws_decode": [vp, i32, i32, i32, vp, vp],
                 "qp_ws_decode_walk": [vp, i32, i32, i32, vp, vp, vp],
                 "qp_ws_infer": [vp, P(qp_field), vp, vp, vp, vp],
@@ -487,6 +492,42 @@ def qp_ws_train_step(m: WarmStartModel, feats, labels, steps, lr, stream=None) -
     return loss.value
 
 
+QP_WS_STATE_PARAMS, QP_WS_STATE_ADAM_M, QP_WS_STATE_ADAM_V, QP_WS_STATE_GRADS = 0, 1, 2, 3
+QP_WS_BUF_X0, QP_WS_BUF_H1, QP_WS_BUF_H2, QP_WS_BUF_H3, QP_WS_BUF_Z, QP_WS_BUF_DZ = 0, 1, 2, 3, 4, 5
+QP_WS_BUF_DH1, QP_WS_BUF_DH2, QP_WS_BUF_DH3, QP_WS_BUF_W_BF16, QP_WS_BUF_WT_BF16 = 6, 7, 8, 16, 32
+
+
+def qp_ws_get_state(m: WarmStartModel, which: int) -> np.ndarray:
+    """fp32 master parameters, Adam moments or last gradients (flat get/set layout)."""
+    out = np.zeros(qp_ws_param_count(), np.float32)
+    _check(lib().qp_ws_get_state(m.ptr, int(which), _ptr(out)))
+    return out
+
+
+def qp_ws_get_buffer(m: WarmStartModel, which: int, rows: int = 0) -> np.ndarray:
+    """Rows of an activation / gradient buffer of the last pass (bf16 buffers as
+    uint16 bits, Z as float32), or a layer's bf16 weight copy (uint16 bits)."""
+    dims = [(256, 16), (256, 256), (256, 256), (256, 256)]
+    if which >= QP_WS_BUF_WT_BF16:
+        no, ni = dims[which - QP_WS_BUF_WT_BF16]
+        out = np.zeros((ni, no), np.uint16)
+    elif which >= QP_WS_BUF_W_BF16:
+        no, ni = dims[which - QP_WS_BUF_W_BF16]
+        out = np.zeros((no, ni), np.uint16)
+    elif which == QP_WS_BUF_Z:
+        out = np.zeros((rows, WS_STEPS), np.float32)
+    else:
+        out = np.zeros((rows, WS_FEATURES if which == QP_WS_BUF_X0 else 256), np.uint16)
+    _check(lib().qp_ws_get_buffer(m.ptr, int(which), int(rows), _ptr(out)))
+    return out
+
+
+def bf16_bits_to_float(u) -> np.ndarray:
+    """uint16 bfloat16 bit patterns -> float64 values."""
+    u = np.asarray(u, np.uint16).astype(np.uint32) << 16
+    return u.view(np.float32).astype(np.float64)
+
+
 def qp_ws_decode(logits, C, start_cell):
     """-> (state uint8 [C*C], path int32 [C])"""
     L = np.ascontiguousarray(logits, np.float32)
@@ -518,6 +559,29 @@ def qp_ws_infer(m: WarmStartModel, field, d=None, stream=None):
     dd = None if d is None else np.ascontiguousarray(d, np.int32)
     _check(lib().qp_ws_infer(m.ptr, ct.byref(f), _ptr(dd), _ptr(st), _ptr(path), _stream(stream)))
     return st, path
+
+
+def qp_ws_expected_steps(logits, steps, E_out=None, stream=None):
+    """Expected step per row of device logits [M, ld] over the first steps[m]
+    entries (device int32 [M]); -> E (device float32 [M])."""
+    import torch
+    M, ld = logits.shape
+    E = torch.empty(M, dtype=torch.float32, device=logits.device) if E_out is None else E_out
+    _check(lib().qp_ws_expected_steps(_ptr(logits), int(ld), int(M), _ptr(steps), _ptr(E), _stream(stream)))
+    return E
+
+
+def qp_ws_walk(h: Handle, score=None, slack=0, state_out=None, path_out=None, length_out=None, stream=None):
+    """The walk decode on the device: -> (state uint8 [C*C], path int32 [C],
+    length int64 [1]), device tensors (allocated when not given)."""
+    import torch
+    C = h.info["C"]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st = torch.empty(C * C, dtype=torch.uint8, device=dev) if state_out is None else state_out
+    pa = torch.empty(C, dtype=torch.int32, device=dev) if path_out is None else path_out
+    ln = torch.empty(1, dtype=torch.int64, device=dev) if length_out is None else length_out
+    _check(lib().qp_ws_walk(h.ptr, _ptr(score), int(slack), _ptr(st), _ptr(pa), _ptr(ln), _stream(stream)))
+    return st, pa, ln
 
 
 def qp_selftest_wait() -> dict:

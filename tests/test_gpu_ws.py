@@ -1,5 +1,7 @@
 """The warm-start MLP on the GPU (tcgen05 GEMMs) against the CPU reference:
-logits within 2e-2 max-abs, gradients within 1e-2 relative per tensor."""
+logits within 2e-2 max-abs, gradients element by element within the bf16
+tolerance of tests/ws_bounds.py (the training pass is also checked tensor by
+tensor on the GPU's own operands in test_gpu_ws_train.py)."""
 import numpy as np
 import pytest
 
@@ -7,6 +9,7 @@ from conftest import has_gpu
 from oracle import mlp_ref
 from paper_2608_25376_gb300 import build as qbuild
 from paper_2608_25376_gb300 import inputs, qpath
+from ws_bounds import grad_error_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -52,11 +55,9 @@ def test_gradients_match_cpu(dev):
     loss, g = qpath.qp_ws_grads(m, X, Y, T)
     ref_loss, ref_g = mlp_ref.loss_and_grads(params, X, Y, T, bf16_storage=True)
     assert abs(loss - ref_loss) <= 1e-3 * abs(ref_loss)
-    offs = np.cumsum([0] + [x for (no, ni) in mlp_ref.DIMS for x in (no * ni, no)])
-    for k in range(len(offs) - 1):
-        a, b = g[offs[k]:offs[k + 1]], ref_g[offs[k]:offs[k + 1]]
-        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-        assert rel <= 1e-2, (k, rel)
+    tol = grad_error_bound(params, X, Y, T)
+    bad = np.abs(g - ref_g) > tol
+    assert not bad.any(), (int(bad.sum()), np.argwhere(bad)[:5])
     # and against the exact float64 network, looser (bf16 storage in between)
     _, g64 = mlp_ref.loss_and_grads(params, X, Y, T, bf16_storage=False)
     rel = np.linalg.norm(g - g64) / np.linalg.norm(g64)
@@ -75,7 +76,7 @@ def test_large_batch_split_k(dev):
     assert np.abs(got[rows] - ref).max() <= 2e-2
     loss, g = qpath.qp_ws_grads(m, X, Y, T)
     ref_loss, ref_g = mlp_ref.loss_and_grads(params, X, Y, T, bf16_storage=True)
-    assert np.linalg.norm(g - ref_g) / np.linalg.norm(ref_g) <= 1e-2
+    assert not (np.abs(g - ref_g) > grad_error_bound(params, X, Y, T)).any()
 
 
 def test_training_reduces_loss(dev):
