@@ -98,15 +98,18 @@ enum { QP_DENSE = 1, QP_STRUCTURED = 2, QP_DIST_I16 = 4 };
  * row-parallel kernel (up to 512 cells), STRUCTURED_FLAT the general structured
  * kernel (up to 4096 cells), STRUCTURED_GROUP the grouped kernel that anneals 4
  * replicas per warp up to 64 cells and 2 up to 128 (faster than the
- * row-parallel kernel at low temperature, slower at high temperature).  All
- * give the same results. */
+ * row-parallel kernel at low temperature, slower at high temperature).  Above
+ * 256 cells the row-parallel kernel keeps each replica's spins in global
+ * memory (more replicas resident per SM); STRUCTURED_ROWS_SHARED forces the
+ * variant with the spins in shared memory.  All give the same results. */
 enum {
   QP_KERNEL_AUTO = 0,
   QP_KERNEL_DENSE = 1,
   QP_KERNEL_STRUCTURED = 2,
   QP_KERNEL_STRUCTURED_FLAT = 3,
   QP_KERNEL_STRUCTURED_ROWS = 4,
-  QP_KERNEL_STRUCTURED_GROUP = 5
+  QP_KERNEL_STRUCTURED_GROUP = 5,
+  QP_KERNEL_STRUCTURED_ROWS_SHARED = 6
 };
 
 /* qp_anneal_opts.flags.  QP_ANNEAL_SKIP_SETTLED lets the row-parallel kernel

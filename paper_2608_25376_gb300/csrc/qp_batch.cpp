@@ -56,6 +56,9 @@ extern "C" qp_status qp_batch_create(qp_handle *const *hs, int32_t count, int32_
     if (!is_device_ptr(states_out[f]) || !is_device_ptr(energies_out[f]) ||
         (best_out && best_out[f] && !is_device_ptr(best_out[f])))
       return fail(QP_EINVAL, "field %d: batch outputs must be device memory", f);
+    QP_DEV_FITS(states_out[f], (size_t)R * h->n, "states_out[f]");
+    QP_DEV_FITS(energies_out[f], (size_t)R * 8, "energies_out[f]");
+    if (best_out) QP_DEV_FITS(best_out[f], (size_t)R * 8, "best_out[f]");
     Cmax = std::max(Cmax, (int)h->C);
   }
   int W = o.replicas_per_cta > 0 ? o.replicas_per_cta : 4;

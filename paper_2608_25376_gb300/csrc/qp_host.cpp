@@ -482,7 +482,15 @@ namespace host {
 // field fits it, else the flat kernel (spins in global memory when a
 // replica's bitset does not fit shared memory comfortably).
 qp_status launch_structured_auto(qp_handle *h, StructArgs &a, int W, bool allow_rows, cudaStream_t st,
-                                 LaunchInfo *info) {
+                                 LaunchInfo *info, bool rows_shared_spins) {
+  if (allow_rows && !rows_shared_spins && rows_g_supported(h->C, h->d_i16, 1)) {
+    int Wg = W > 0 ? W : rows_g_auto_warps(h->C, h->d_i16, a.R);
+    while (Wg > 1 && !rows_g_supported(h->C, h->d_i16, Wg)) --Wg;
+    QP_TRY(h->gstate.ensure((size_t)a.R * rows_g_words(h->C) * 4));
+    a.gstate = h->gstate.as<uint32_t>();
+    QP_CU(launch_rows_g(a, h->d_i16, Wg, st, info));
+    return QP_OK;
+  }
   if (allow_rows) {
     int Wr = W > 0 ? W : rows_auto_warps(h->C, h->d_i16, a.R);
     while (Wr > 1 && !rows_supported(h->C, h->d_i16, Wr)) --Wr;
@@ -521,7 +529,8 @@ extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc
   int kernel = o.kernel;
   if (kernel == QP_KERNEL_AUTO) kernel = h->path ? QP_KERNEL_STRUCTURED : QP_KERNEL_DENSE;
   const bool structured = kernel == QP_KERNEL_STRUCTURED || kernel == QP_KERNEL_STRUCTURED_FLAT ||
-                          kernel == QP_KERNEL_STRUCTURED_ROWS || kernel == QP_KERNEL_STRUCTURED_GROUP;
+                          kernel == QP_KERNEL_STRUCTURED_ROWS || kernel == QP_KERNEL_STRUCTURED_GROUP ||
+                          kernel == QP_KERNEL_STRUCTURED_ROWS_SHARED;
   if (structured && !h->path) return fail(QP_EINVAL, "no structured form in this handle");
   if (kernel == QP_KERNEL_DENSE && !h->has_dense) return fail(QP_EINVAL, "handle was built without QP_DENSE");
   if (!structured && kernel != QP_KERNEL_DENSE) return fail(QP_EINVAL, "unknown kernel %d", kernel);
@@ -535,6 +544,11 @@ extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc
   QP_TRY(device_schedule(*sc, &sched, &sched_keep));
   const size_t n = (size_t)h->n;
 
+  QP_DEV_FITS(init, (size_t)R * n, "init_states");
+  QP_DEV_FITS(states_out, (size_t)R * n, "states_out");
+  QP_DEV_FITS(energies_out, (size_t)R * 8, "energies_out");
+  QP_DEV_FITS(best_out, (size_t)R * 8, "best_out");
+  QP_DEV_FITS(o.accepts_out, (size_t)R * 8, "accepts_out");
   // stage host buffers
   const uint8_t *init_d = init;
   if (init && !is_device_ptr(init)) {
@@ -576,7 +590,8 @@ extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc
       goto launched;
     }
     // replicas per CTA as asked, else chosen for the most resident chains
-    QP_TRY(launch_structured_auto(h, a, o.replicas_per_cta, kernel != QP_KERNEL_STRUCTURED_FLAT, st, &info));
+    QP_TRY(launch_structured_auto(h, a, o.replicas_per_cta, kernel != QP_KERNEL_STRUCTURED_FLAT, st, &info,
+                                  kernel == QP_KERNEL_STRUCTURED_ROWS_SHARED));
   } else {
     int W = o.replicas_per_cta ? o.replicas_per_cta : 4;
     while (W > 1 && !dense_h_fits_smem(h->n, h->path ? h->C : 0, W)) --W;
@@ -665,6 +680,9 @@ extern "C" qp_status qp_decode_batch(const qp_handle *hc, int32_t R, const uint8
   DevSet ds(h->dev);
   cudaStream_t st = static_cast<cudaStream_t>(stream_);
   const size_t n = (size_t)h->n;
+  QP_DEV_FITS(states, (size_t)R * n, "states");
+  QP_DEV_FITS(paths_out, (size_t)R * h->C * 4, "paths_out");
+  QP_DEV_FITS(lengths_out, (size_t)R * 8, "lengths_out");
   const uint8_t *sd = states;
   bool sync = false;
   if (!is_device_ptr(states)) {
@@ -729,6 +747,35 @@ qp_status set_error(qp_status s, const char *msg) { return fail(s, "%s", msg); }
 void clear_error() { g_err.clear(); }
 
 bool device_pointer(const void *p) { return is_device_ptr(p); }
+
+namespace {
+using GetAddressRange = int (*)(unsigned long long *, size_t *, unsigned long long);
+GetAddressRange address_range_fn() {
+  static std::once_flag once;
+  static GetAddressRange fn = nullptr;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<GetAddressRange>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+}  // namespace
+
+bool device_range_fits(const void *p, size_t bytes) {
+  if (!p || bytes == 0) return true;
+  GetAddressRange fn = address_range_fn();
+  if (!fn) return true;
+  unsigned long long base = 0;
+  size_t size = 0;
+  const unsigned long long a = reinterpret_cast<uintptr_t>(p);
+  if (fn(&base, &size, a) != 0) return true;  // not an allocation the driver knows: cannot tell
+  return a >= base && a - base <= size && bytes <= size - (a - base);
+}
 
 }  // namespace qp
 

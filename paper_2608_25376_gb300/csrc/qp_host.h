@@ -23,6 +23,15 @@ extern thread_local std::string g_err;
 // Record a printf-style message and return s.
 qp_status fail(qp_status s, const char *fmt, ...);
 
+// A caller's device buffer smaller than the call needs is refused before any
+// launch (QP_EINVAL) when the driver can see it.
+#define QP_DEV_FITS(p, bytes, what)                                                            \
+  do {                                                                                          \
+    if ((p) && ::qp::host::is_device_ptr(p) && !::qp::device_range_fits((p), (bytes)))          \
+      return ::qp::host::fail(QP_EINVAL, "%s: the device buffer is smaller than the %zu bytes " \
+                              "the call needs", (what), (size_t)(bytes));                       \
+  } while (0)
+
 #define QP_CU(call)                                                                    \
   do {                                                                                 \
     cudaError_t e_ = (call);                                                           \
@@ -132,6 +141,6 @@ namespace host {
 // field fits it, else the flat kernel.
 // W = replicas per CTA, 0 = chosen from the occupancy (row kernel) or 4 (flat kernel)
 qp_status launch_structured_auto(qp_handle *h, StructArgs &a, int W, bool allow_rows, cudaStream_t st,
-                                 LaunchInfo *info);
+                                 LaunchInfo *info, bool rows_shared_spins = false);
 }  // namespace host
 }  // namespace qp

@@ -90,6 +90,13 @@ bool rows_supported(int C, bool d_i16, int warps_per_cta);
 // Replicas per CTA for the row kernel that keep the most chains resident on
 // the GPU at once (R replicas in all); memoised per device and shape.
 int rows_auto_warps(int C, bool d_i16, int R);
+// The row kernel with the spins in global memory (fields of 257..512 cells):
+// words of one replica's row bitsets, support, occupancy choice, launch
+// (a.gstate: R x rows_g_words(C) words).
+size_t rows_g_words(int C);
+bool rows_g_supported(int C, bool d_i16, int warps_per_cta);
+int rows_g_auto_warps(int C, bool d_i16, int R);
+cudaError_t launch_rows_g(const StructArgs &a, bool d_i16, int warps_per_cta, cudaStream_t st, LaunchInfo *info);
 cudaError_t launch_rows(const StructArgs &a, bool d_i16, int warps_per_cta, cudaStream_t st,
                         LaunchInfo *info);
 // Batched persistent launch (qp_sweep_rows.cu): fields[] per field, units[]
@@ -149,6 +156,11 @@ bool schedule_lookup(const qp_schedule &sc, DeviceSchedule *out, std::shared_ptr
 qp_status set_error(qp_status s, const char *msg);
 void clear_error();  // empties this thread's qp_last_error message
 bool device_pointer(const void *p);
+// True when the caller's device buffer [p, p + bytes) lies inside the one
+// allocation that holds p (cuMemGetAddressRange), or when the driver cannot
+// tell (p not in its allocation tables).  A pooling allocator's buffer lies
+// inside a larger block, so only overruns past that block are caught.
+bool device_range_fits(const void *p, size_t bytes);
 
 // Makes the current device load the module that holds qp_anneal_noalloc's
 // fixed scratch array (the driver allocates the array at that moment; CUDA

@@ -68,6 +68,10 @@ extern "C" qp_status qp_anneal_noalloc(qp_handle *h, int32_t R, const qp_schedul
   if (!device_pointer(states_out) || !device_pointer(energies_out) || (best_out && !device_pointer(best_out)) ||
       (init && !device_pointer(init)))
     return set_error(QP_EINVAL, "qp_anneal_noalloc: every buffer must be device memory");
+  const size_t n = (size_t)v.C * v.C;
+  if (!device_range_fits(states_out, (size_t)R * n) || !device_range_fits(energies_out, (size_t)R * 8) ||
+      (best_out && !device_range_fits(best_out, (size_t)R * 8)) || (init && !device_range_fits(init, (size_t)R * n)))
+    return set_error(QP_EINVAL, "qp_anneal_noalloc: a device buffer is smaller than the call needs");
   DeviceSchedule sched;
   std::shared_ptr<const void> sched_keep;  // the tables stay alive until the launch is queued
   if (!schedule_lookup(*sc, &sched, &sched_keep))

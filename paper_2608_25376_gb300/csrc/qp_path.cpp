@@ -28,6 +28,10 @@ extern "C" qp_status qp_repair_batch(const qp_handle *hc, int32_t R, const uint8
   DevSet ds(h->dev);
   cudaStream_t st = static_cast<cudaStream_t>(stream_);
   const size_t n = (size_t)h->n;
+  QP_DEV_FITS(states, (size_t)R * n, "states");
+  QP_DEV_FITS(paths_out, (size_t)R * h->C * 4, "paths_out");
+  QP_DEV_FITS(lengths_out, (size_t)R * 8, "lengths_out");
+  QP_DEV_FITS(status_out, (size_t)R * 4, "status_out");
   const uint8_t *sd = states;
   bool sync = false;
   if (!is_device_ptr(states)) {

@@ -95,6 +95,12 @@ extern "C" qp_status qp_anneal_pt(qp_handle *h, int32_t G, const qp_pt_schedule 
   const int32_t *xlen = nullptr;
   QP_TRY(exchange_tables(ladder, &xthr, &xoff, &xlen));
   const size_t n = (size_t)h->n;
+  QP_DEV_FITS(init, (size_t)R * n, "init_states");
+  QP_DEV_FITS(states_out, (size_t)R * n, "states_out");
+  QP_DEV_FITS(energies_out, (size_t)R * 8, "energies_out");
+  QP_DEV_FITS(best_out, (size_t)R * 8, "best_out");
+  QP_DEV_FITS(levels_out, (size_t)R * 4, "levels_out");
+  QP_DEV_FITS(swaps_out, (size_t)G * (M - 1) * 8, "swaps_out");
   QP_TRY(h->pt_states[0].ensure((size_t)R * n));
   QP_TRY(h->pt_states[1].ensure((size_t)R * n));
   QP_TRY(h->pt_E.ensure((size_t)R * 8));

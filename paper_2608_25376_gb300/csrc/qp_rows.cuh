@@ -52,12 +52,21 @@ __device__ __forceinline__ void set_drow(const void *d, int Cp, int C, int h, in
   }
 }
 
+// A word of a replica's spins: from shared memory, or, with SG (spins in
+// global memory, flipped by atomics in L2), from L2 past the L1 cache, which
+// could still hold the line as it was before the flip.
+template <bool SG>
+__device__ __forceinline__ uint32_t spin_word(const uint32_t *p) {
+  if (SG) return __ldcg(p);
+  return *p;
+}
+
 // F += sum over the set bits h of one row of d[h][.]; returns the number of bits
 // and, in *one, the cell when there is exactly one (else -1).
-template <typename DT, int NCH, int DMODE>
+template <typename DT, int NCH, int DMODE, bool SG = false>
 __device__ __forceinline__ int scan_row_field(const uint32_t *row, int Cw, const void *d, int Cp, int C,
                                               int lane, int (&F)[NCH][4], int *one) {
-  const uint32_t word = lane < Cw ? row[lane] : 0u;
+  const uint32_t word = lane < Cw ? spin_word<SG>(row + lane) : 0u;
   const int cnt = __reduce_add_sync(kFull, __popc(word));
   uint32_t bal = __ballot_sync(kFull, word != 0u);
   int last = -1;
@@ -88,8 +97,9 @@ __device__ __forceinline__ void row_field(const uint32_t *st, int Cw, const int1
 }
 
 // The single hot cell of a row, or -1 if the row does not hold exactly one.
+template <bool SG = false>
 __device__ __forceinline__ int row_single(const uint32_t *row, int Cw, int lane) {
-  const uint32_t word = lane < Cw ? row[lane] : 0u;
+  const uint32_t word = lane < Cw ? spin_word<SG>(row + lane) : 0u;
   const int cnt = __reduce_add_sync(kFull, __popc(word));
   if (cnt != 1) return -1;
   const uint32_t bal = __ballot_sync(kFull, word != 0u);
@@ -113,8 +123,9 @@ __device__ __forceinline__ int sel4(const int (&v)[4], int j) {
 // The proposals of one 128-wide row chunk when at least one of them can be
 // accepted or needs a draw: evaluate against the current row sum, take the
 // first accepted one, apply it, resume after it.  Returns whether any flip was
-// applied.
-template <typename DT, int NCH, int DMODE>
+// applied.  SG: the row's bits are in global memory (flipped by a fire-and-
+// forget atomic XOR, so the warp never waits on the write).
+template <typename DT, int NCH, int DMODE, bool SG = false>
 __device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int (&base)[4], const int (&de0)[4],
                                        int &xnc, int validc,
                                        int (&tAc)[4], int &rt, int (&Cu)[NCH][4], uint32_t *row, long long &E,
@@ -193,7 +204,9 @@ __device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int
       for (int j = 0; j < 4; ++j)
         if (j == jj) tAc[j] += dlt * twoA;
       xnc ^= 1 << jj;
-      row[QP_IX(4 * c + (L >> 3), (C + 31) >> 5, 3)] ^= 1u << (4 * (L & 7) + jj);
+      const int wi = QP_IX(4 * c + (L >> 3), (C + 31) >> 5, 3);
+      if (SG) atomicXor(row + wi, 1u << (4 * (L & 7) + jj));
+      else row[wi] ^= 1u << (4 * (L & 7) + jj);
     }
     add_drow<DT, NCH, DMODE>(d, Cp, C, 128 * c + 4 * L + jj, lane, dlt, Cu);
     cand &= lane < L ? 0 : (lane > L ? 0xF : (0xF << (jj + 1)) & 0xF);
@@ -208,9 +221,11 @@ __device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int
 
 
 // The initial state of replica r (given or all zero, with row 0 and column s
-// clamped: x_{0,s} = 1), its single-cell cache, 2A x column sums, the mask
-// of proposable columns, its energy by Eqs. 3-6 and its violation count.
-template <typename DT, int NCH, int DMODE>
+// clamped: x_{0,s} = 1), its single-cell cache (the cell when a row holds
+// exactly one, -1 when it holds none, -2 when it holds several), 2A x column
+// sums, the mask of proposable columns, its energy by Eqs. 3-6 and its
+// violation count.
+template <typename DT, int NCH, int DMODE, bool SG = false>
 __device__ __forceinline__ void rows_init(const StructArgs &a, int r, uint32_t *st, int16_t *hot1, const void *d,
                                           int lane, int (&tAc)[NCH][4], int (&validc)[NCH], long long &E_out,
                                           int &viol_out) {
@@ -257,7 +272,7 @@ __device__ __forceinline__ void rows_init(const StructArgs &a, int r, uint32_t *
 #pragma unroll
       for (int c = 0; c < NCH; ++c) {
         const int ib = 128 * c + 4 * lane;
-        xb[c] = ib < C ? (int)((row[4 * c + (lane >> 3)] >> (4 * (lane & 7))) & 0xFu) : 0;
+        xb[c] = ib < C ? (int)((spin_word<SG>(row + 4 * c + (lane >> 3)) >> (4 * (lane & 7))) & 0xFu) : 0;
         rsum += __popc(xb[c]);
 #pragma unroll
         for (int j = 0; j < 4; ++j) cs[c][j] += (xb[c] >> j) & 1;
@@ -265,12 +280,12 @@ __device__ __forceinline__ void rows_init(const StructArgs &a, int r, uint32_t *
       rsum = __reduce_add_sync(kFull, rsum);
       pen_rows += (long long)(1 - rsum) * (1 - rsum);
       viol += rsum != 1;
-      const int h1 = row_single(row, Cw, lane);
-      if (lane == 0) hot1[t] = (int16_t)h1;
+      const int h1 = row_single<SG>(row, Cw, lane);
+      if (lane == 0) hot1[t] = (int16_t)(rsum == 1 ? h1 : (rsum == 0 ? -1 : -2));
       if (t + 1 < C) {
         zero<NCH>(Fn);
         int one;
-        scan_row_field<DT, NCH, DMODE>(st + (t + 1) * Cw, Cw, d, Cp, C, lane, Fn, &one);
+        scan_row_field<DT, NCH, DMODE, SG>(st + (t + 1) * Cw, Cw, d, Cp, C, lane, Fn, &one);
 #pragma unroll
         for (int c = 0; c < NCH; ++c)
 #pragma unroll

@@ -215,6 +215,236 @@ __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_
 }
 
 
+// ---------------------------------------------------------------------------
+// Wide fields whose distance matrix lives in L2 (more than 256 cells, d not in
+// shared memory): the same chain with the spins in global memory.  A replica's
+// C x Cw row bitsets take 31 KB at 491 cells, and in shared memory they held
+// the SM to 7 replicas; here shared memory keeps only, per replica, the
+// single-cell cache hot[t] (the cell when row t holds exactly one, -1 when it
+// holds none, -2 when it holds several) and a ring of K distance rows that
+// cp.async fills K-1 rows ahead of use, so the L2 latency of d stays off the
+// row's dependent chain.  A row that holds one cell or none needs no bits at
+// all: its four-bit groups and sum follow from hot[t]; only rows with several
+// cells read their bits (from L2).  Flips reach the bits by atomic XOR (no
+// wait); the cache of a flipped row is rebuilt from the lanes' registers.
+
+// cp.async (global -> shared, BYTES = 4, 8 or 16), group commit and wait
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst, const void *src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// The field of row u for the global-spins kernel: the d row of its single
+// cell, zero for an empty row, a scan of its bits (from L2) otherwise.
+template <typename DT, int NCH>
+__device__ __forceinline__ void field_g(const uint32_t *st, int Cw, int code, int u, const void *d, int Cp, int C,
+                                        int lane, int (&F)[NCH][4]) {
+  if (code >= 0) set_drow<DT, NCH, 0>(d, Cp, C, code, lane, F);
+  else {
+    zero<NCH>(F);
+    if (code == -2) { int one; scan_row_field<DT, NCH, 0, true>(st + (size_t)u * Cw, Cw, d, Cp, C, lane, F, &one); }
+  }
+}
+
+template <typename DT, int NCH, int K>
+__device__ __forceinline__ void ring_issue(const int16_t *hot, DT *ring, const void *d, int Cp, int C, int u,
+                                           int lane) {
+  if (u >= C) return;
+  const int h = hot[u];
+  if (h < 0) return;
+  DT *slot = ring + (size_t)(u % K) * Cp;
+  const DT *src = static_cast<const DT *>(d) + (size_t)QP_IX(h, C, 2) * Cp;
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    const int i = 128 * c + 4 * lane;
+    if (i < C) cp_async<4 * (int)sizeof(DT)>(slot + i, src + i);
+  }
+}
+
+template <typename DT, int NCH, int K>
+__device__ __forceinline__ void rows_replica_g(const StructArgs &a, int r, uint32_t *st, int16_t *hot, DT *ring,
+                                               int lane) {
+  static_assert(K >= 3, "the ring holds rows t+2 .. t+K+1");
+  const int C = a.C, Cp = a.Cp, s0 = a.start, A = a.A, B = a.B;
+  const int twoA = 2 * A;
+  const int Cw = (C + 31) >> 5;
+  const int n = C * C;
+  const uint32_t rg = (uint32_t)(a.rep_offset + r);
+  const void *d = a.d;
+
+  int tAc[NCH][4];
+  int validc[NCH];
+  long long E;
+  int viol;
+  rows_init<DT, NCH, 0, true>(a, r, st, hot, d, lane, tAc, validc, E, viol);
+  long long best = LLONG_MAX, acc = 0;
+
+  const int lev = a.level ? __ldg(a.level + r) : -1;
+  bool settled = false;
+  int settled_len = 0;
+  for (int s = a.sweep_begin; s < a.sweep_end; ++s) {
+    const int ts = lev >= 0 ? lev : s;
+    const uint32_t *thr = a.thr + a.thr_off[ts];
+    const int len = a.thr_len[ts];
+    if (settled && len <= settled_len) continue;
+    bool any_hit = false;
+    const unsigned lenm1 = (unsigned)(len - 1);
+    const float cT = a.thr_c[ts];
+    const int dq = len > 1 ? min(len - 1, max(1, (int)fminf(8.0f / cT, 1.0e9f))) : 1;
+    const uint32_t Q = len > 1 ? __ldg(a.thr + a.thr_off[ts] + dq) : 0u;
+    // P, Cu, N: the fields of rows t-1, t, t+1; Nn: row t+2's, read from the
+    // ring one row ahead
+    int P[NCH][4], Cu[NCH][4], N[NCH][4], Nn[NCH][4];
+    zero<NCH>(P);
+    add_drow<DT, NCH, 0>(d, Cp, C, s0, lane, 1, P);  // row 0 holds only the start cell
+    field_g<DT, NCH>(st, Cw, hot[1], 1, d, Cp, C, lane, Cu);
+    if (C > 2) field_g<DT, NCH>(st, Cw, hot[2], 2, d, Cp, C, lane, Nn);
+    else zero<NCH>(Nn);
+    // the ring holds rows t+2 .. t+K+1 while row t runs; rows 3 .. K+1 first
+    for (int u = 3; u <= K + 1; ++u) {
+      ring_issue<DT, NCH, K>(hot, ring, d, Cp, C, u, lane);
+      cp_async_commit();
+    }
+    int hn = hot[1];
+    for (int t = 1; t < C; ++t) {
+      uint32_t *row = st + (size_t)t * Cw;
+#pragma unroll
+      for (int c = 0; c < NCH; ++c)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) N[c][j] = Nn[c][j];
+      if (t + 2 < C) {
+        cp_async_wait<K - 2>();  // row t+2's copy (issued K-1 rows ago) has landed
+        const int h2 = hot[t + 2];
+        if (h2 >= 0) set_drow<DT, NCH, 1>(ring + (size_t)((t + 2) % K) * Cp, Cp, C, 0, lane, Nn);
+        else field_g<DT, NCH>(st, Cw, h2, t + 2, d, Cp, C, lane, Nn);
+      } else {
+        zero<NCH>(Nn);  // past the last row
+      }
+      // row t+K+1 into the slot row t+1 has left (its data is in N now)
+      ring_issue<DT, NCH, K>(hot, ring, d, Cp, C, t + K + 1, lane);
+      cp_async_commit();
+      // row t's bits and sum: from the cache when it holds one cell or none
+      int xn[NCH];
+      int rt;
+      if (hn >= 0) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) xn[c] = (hn >> 2) == 32 * c + lane ? 1 << (hn & 3) : 0;
+        rt = 1;
+      } else if (hn == -1) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) xn[c] = 0;
+        rt = 0;
+      } else {
+        rt = 0;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+          xn[c] = 128 * c + 4 * lane < C ? (int)((__ldcg(row + 4 * c + (lane >> 3)) >> (4 * (lane & 7))) & 0xFu) : 0;
+          rt += __popc(xn[c]);
+        }
+        rt = __reduce_add_sync(kFull, rt);
+      }
+      const int hn_next = t + 1 < C ? hot[t + 1] : -1;
+      const int rt0 = rt;
+      bool flipped = false;
+      const int tC = t * C;
+      bool maybe = false;
+      {
+        const int lo = len - twoA * (rt - 1), hi = twoA * (3 - rt) - len;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+          if (128 * c >= C) break;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int b = B * (P[c][j] + N[c][j]) + tAc[c][j];
+            maybe |= (b < lo) | (b > hi);
+          }
+        }
+      }
+      if (__any_sync(kFull, maybe)) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+          if (128 * c >= C) break;
+          int base[4], de[4];
+          unsigned hit = 0;
+          {
+            const int k0 = twoA * (rt - 1), k1 = twoA * (3 - rt);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              base[j] = B * (P[c][j] + N[c][j]) + tAc[c][j];
+              de[j] = ((xn[c] >> j) & 1) ? k1 - base[j] : base[j] + k0;
+              hit |= (unsigned)(de[j] < len) << j;
+            }
+          }
+          if (__any_sync(kFull, hit & validc[c])) {
+            any_hit = true;
+            flipped |= row_chunk<DT, NCH, 0, true>(c, t, s, tC, base, de, xn[c], validc[c], tAc[c], rt, Cu, row,
+                                                   E, acc, viol, d, Cp, C, lane, twoA, len, lenm1, cT, dq, Q, thr,
+                                                   rg, a.key0, a.key1);
+          }
+        }
+      }
+      viol += (rt != 1) - (rt0 != 1);
+      if (flipped) {
+        int code = rt == 0 ? -1 : -2;
+        if (rt == 1) {
+          int mine = -1;
+#pragma unroll
+          for (int c = 0; c < NCH; ++c)
+            if (xn[c]) mine = 128 * c + 4 * lane + __ffs(xn[c]) - 1;
+          const unsigned bal = __ballot_sync(kFull, mine >= 0);
+          code = __shfl_sync(kFull, mine, __ffs(bal) - 1);
+        }
+        if (lane == 0) hot[t] = (int16_t)code;
+        __syncwarp();
+      }
+#pragma unroll
+      for (int c = 0; c < NCH; ++c)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          P[c][j] = Cu[c][j];
+          Cu[c][j] = N[c][j];
+        }
+      hn = hn_next;
+    }
+    cp_async_wait<0>();  // the next sweep refills every slot
+    __syncwarp();
+    if (viol == 0 && E < best) best = E;
+    settled = a.skip_settled && !any_hit;
+    settled_len = len;
+  }
+
+  uint8_t *out = a.states_out + (size_t)r * n;
+  for (int e = lane; e < n; e += 32) {
+    const int t = e / C, i = e - t * C;
+    out[e] = (uint8_t)((__ldcg(st + (size_t)t * Cw + (i >> 5)) >> (i & 31)) & 1u);
+  }
+  if (lane == 0) {
+    a.E_out[r] = E;
+    if (a.best_out) a.best_out[r] = best;
+    if (a.acc_out) a.acc_out[r] = acc;
+  }
+}
+
+constexpr int kRowsGMaxWarps = 12;  // 384 threads: at most 170 registers per thread
+constexpr int kRowsGRing = 8;
+
+template <typename DT, int NCH>
+__global__ void __launch_bounds__(kRowsGMaxWarps * 32) k_sweep_rows_g(const StructArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const size_t hot_bytes = align16r(2 * (size_t)a.C);
+  const size_t per_warp = hot_bytes + (size_t)kRowsGRing * a.Cp * sizeof(DT);
+  int16_t *hot = reinterpret_cast<int16_t *>(smem + warp * per_warp);
+  DT *ring = reinterpret_cast<DT *>(smem + warp * per_warp + hot_bytes);
+  const int r = blockIdx.x * W + warp;
+  if (r >= a.R) return;
+  rows_replica_g<DT, NCH, kRowsGRing>(a, r, a.gstate + (size_t)r * a.nw_pad, hot, ring, lane);
+}
+
 // Widest rows (NCH = 4) keep three 16-register fields per lane: they get up to
 // 255 registers by capping the CTA at 8 replicas.
 template <int NCH>
@@ -398,6 +628,97 @@ int rows_blocks_per_sm(int C, bool d_i16, int W) {
 }
 
 }  // namespace
+
+// ---- the global-spins row kernel (fields of 257..512 cells)
+size_t rows_g_words(int C) {
+  const int Cw = (C + 31) / 32;
+  return (size_t)(C * Cw + 3) / 4 * 4;
+}
+
+size_t rows_g_smem(int C, bool d_i16, int W) {
+  const int Cp = (C + 7) / 8 * 8;
+  return (size_t)W * (align16r(2 * (size_t)C) + (size_t)kRowsGRing * Cp * (d_i16 ? 2 : 4));
+}
+
+bool rows_g_supported(int C, bool d_i16, int W) {
+  return C > 256 && C <= 512 && W >= 1 && W <= kRowsGMaxWarps && rows_g_smem(C, d_i16, W) <= kSmemLimitRows;
+}
+
+namespace {
+
+template <typename DT>
+cudaError_t occ_g(int W, size_t smem, int *blocks) {
+  auto k = k_sweep_rows_g<DT, 4>;
+  std::lock_guard<std::mutex> lk(launch_mutex());
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, W * 32, smem);
+}
+
+}  // namespace
+
+int rows_g_auto_warps(int C, bool d_i16, int R) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 4;
+  }
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, bool, int>, int> memo;
+  const auto key = std::make_tuple(dev, C, d_i16, R);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = memo.find(key);
+    if (it != memo.end()) return it->second;
+  }
+  // the most replicas resident at once; among equals the larger CTA
+  int best_w = 1;
+  long long best = -1;
+  for (int W = 1; W <= kRowsGMaxWarps; ++W) {
+    if (!rows_g_supported(C, d_i16, W)) continue;
+    int b = 0;
+    const cudaError_t e = d_i16 ? occ_g<int16_t>(W, rows_g_smem(C, d_i16, W), &b)
+                                : occ_g<int32_t>(W, rows_g_smem(C, d_i16, W), &b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    const long long resident = std::min<long long>(R, (long long)sms * b * W);
+    if (resident >= best) {
+      best = resident;
+      best_w = W;
+    }
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  memo[key] = best_w;
+  return best_w;
+}
+
+cudaError_t launch_rows_g(const StructArgs &a_in, bool d_i16, int W, cudaStream_t st, LaunchInfo *info) {
+  StructArgs a = a_in;
+  if (!rows_g_supported(a.C, d_i16, W) || a.gstate == nullptr) return cudaErrorInvalidValue;
+  a.nw_pad = (int32_t)rows_g_words(a.C);
+  const size_t smem = rows_g_smem(a.C, d_i16, W);
+  if (info) {
+    info->warps_per_cta = W;
+    info->blocks = (a.R + W - 1) / W;
+    info->smem = smem;
+    info->variant = "rows,spins:global,d:L2 ring";
+  }
+  std::lock_guard<std::mutex> lk(launch_mutex());
+  cudaError_t e;
+  if (d_i16) {
+    auto k = k_sweep_rows_g<int16_t, 4>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) k<<<(a.R + W - 1) / W, W * 32, smem, st>>>(a);
+  } else {
+    auto k = k_sweep_rows_g<int32_t, 4>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) k<<<(a.R + W - 1) / W, W * 32, smem, st>>>(a);
+  }
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
 
 int rows_auto_warps(int C, bool d_i16, int R) {
   int dev = 0, sms = 0;

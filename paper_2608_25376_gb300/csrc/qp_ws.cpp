@@ -345,6 +345,8 @@ extern "C" qp_status qp_ws_set_params(qp_ws *m, const float *in) {
 
 extern "C" qp_status qp_ws_forward(qp_ws *m, const float *feats, int32_t M, float *logits_out, void *stream) {
   if (!m || !feats || !logits_out || M < 1) return set_error(QP_EINVAL, "bad argument");
+  if (device_pointer(logits_out) && !device_range_fits(logits_out, (size_t)M * kOut * 4))
+    return set_error(QP_EINVAL, "qp_ws_forward: the device buffer for the logits is too small");
   DevGuard g(m->dev);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int Mp = (M + 127) / 128 * 128;

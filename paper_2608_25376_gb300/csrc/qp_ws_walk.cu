@@ -132,6 +132,9 @@ extern "C" qp_status qp_ws_expected_steps(const float *logits, int32_t ld, int32
     return set_error(QP_EINVAL, "qp_ws_expected_steps: bad argument");
   if (!device_pointer(logits) || !device_pointer(steps) || !device_pointer(E_out))
     return set_error(QP_EINVAL, "qp_ws_expected_steps: every buffer must be device memory");
+  if (!device_range_fits(logits, (size_t)M * ld * 4) || !device_range_fits(steps, (size_t)M * 4) ||
+      !device_range_fits(E_out, (size_t)M * 4))
+    return set_error(QP_EINVAL, "qp_ws_expected_steps: a device buffer is smaller than the call needs");
   k_expected_step<<<(M + 7) / 8, 256, 0, static_cast<cudaStream_t>(stream)>>>(logits, ld, steps, M, E_out);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(QP_ECUDA, cudaGetErrorString(e));
@@ -151,6 +154,10 @@ extern "C" qp_status qp_ws_walk(qp_handle *h, const float *score, int32_t slack,
   if ((score && !device_pointer(score)) || (state_out && !device_pointer(state_out)) ||
       (path_out && !device_pointer(path_out)) || (length_out && !device_pointer(length_out)))
     return set_error(QP_EINVAL, "qp_ws_walk: every buffer must be device memory");
+  if ((score && !device_range_fits(score, (size_t)v.C * 4)) ||
+      (state_out && !device_range_fits(state_out, (size_t)v.C * v.C)) ||
+      (path_out && !device_range_fits(path_out, (size_t)v.C * 4)) || (length_out && !device_range_fits(length_out, 8)))
+    return set_error(QP_EINVAL, "qp_ws_walk: a device buffer is smaller than the call needs");
   int prev = -1;
   if (cudaGetDevice(&prev) != cudaSuccess) return set_error(QP_ECUDA, "qp_ws_walk: cudaGetDevice failed");
   if (prev != v.dev && cudaSetDevice(v.dev) != cudaSuccess) return set_error(QP_ECUDA, "qp_ws_walk: cudaSetDevice failed");

@@ -21,7 +21,7 @@ _lib = None
 QP_OK, QP_EINVAL, QP_ENOMEM, QP_ERANGE, QP_ECUDA, QP_ETIMEOUT, QP_EINFEASIBLE = range(7)
 QP_DENSE, QP_STRUCTURED, QP_DIST_I16 = 1, 2, 4
 QP_KERNEL_AUTO, QP_KERNEL_DENSE, QP_KERNEL_STRUCTURED, QP_KERNEL_STRUCTURED_FLAT = 0, 1, 2, 3
-QP_KERNEL_STRUCTURED_ROWS, QP_KERNEL_STRUCTURED_GROUP = 4, 5
+QP_KERNEL_STRUCTURED_ROWS, QP_KERNEL_STRUCTURED_GROUP, QP_KERNEL_STRUCTURED_ROWS_SHARED = 4, 5, 6
 QP_ANNEAL_SKIP_SETTLED = 1
 E_NONE = np.iinfo(np.int64).max
 

@@ -7,13 +7,20 @@ Pipeline (all GPU work goes through the C ABI):
                  step in that path.
   2. training -- the per-cell MLP (qp_ws_*) with softmax cross-entropy over the
                  cell's possible steps, Adam, mini-batches of whole fields.
-  3. seeding  -- features -> step logits (tcgen05 forward) -> greedy decode ->
-                 a feasible one-hot state; a fraction of the replicas start from
-                 it at a lower temperature, the rest anneal plainly (fallback).
-  4. judging  -- time until the best feasible path found is within 1% of the
-                 best known path, learned arm vs plain arm, on held-out fields;
-                 runs are split into sweep segments (resumable, bit-identical to
-                 one run) so the best can be read as the run proceeds.
+  3. seeding  -- features -> step logits (tcgen05 forward) -> expected step
+                 per cell -> the device walk (qp_ws_walk: among the unvisited
+                 cells within a slack of the nearest one, the smallest expected
+                 step) -> a feasible one-hot state; a fraction of the replicas
+                 start from it at a lower temperature, the rest anneal plainly
+                 (fallback).
+  4. judging  -- on held-out fields, against a best known path computed first
+                 and independently of the arms (long plain anneals, every final
+                 state repaired with 2-opt): the time (and the sweeps) until an
+                 arm's best path is within 1% of it, for plain annealing, the
+                 same seeding with no network (the nearest-cell walk), with an
+                 untrained network and with the trained one.  Runs are split
+                 into sweep segments (resumable, bit-identical to one run) so the
+                 best can be read as the run proceeds.
 """
 from __future__ import annotations
 
@@ -39,11 +46,14 @@ def mixing_penalty(C: int) -> int:
 
 # ----------------------------------------------------------------------------- 1. labels
 def annealer_labels(fields, replicas=32, n_sweeps=2000, seed=11, chunk=256, penalty=mixing_penalty,
-                    t0_over_a=0.5, log=None):
+                    t0_over_a=0.5, repair_passes=None, log=None):
     """-> list of (features [C,16] float32, labels [C] int32, length) for the
-    fields whose anneal produced a feasible final state.  Each field is
-    annealed with A = penalty(C) (None: the library default 2 max d) and
-    T0 = t0_over_a * A (1e3 for the default)."""
+    fields whose anneal produced a path.  Each field is annealed with
+    A = penalty(C) (None: the library default 2 max d) and T0 = t0_over_a * A
+    (1e3 for the default).  The label path is the shortest feasible final
+    state, or, with repair_passes set, the shortest of all final states
+    repaired into paths (qp_repair_batch with that many 2-opt passes, -1 =
+    until no move helps)."""
     import torch
     out = []
     for c0 in range(0, len(fields), chunk):
@@ -63,7 +73,11 @@ def annealer_labels(fields, replicas=32, n_sweeps=2000, seed=11, chunk=256, pena
             C = h.info["C"]
             paths = torch.zeros((replicas, C), dtype=torch.int32, device="cuda")
             lens = torch.zeros(replicas, dtype=torch.int64, device="cuda")
-            qpath.qp_decode_batch(h, replicas, s_, paths, lens, stream=torch.cuda.current_stream())
+            if repair_passes is None:
+                qpath.qp_decode_batch(h, replicas, s_, paths, lens, stream=torch.cuda.current_stream())
+            else:
+                qpath.qp_repair_batch(h, replicas, s_, repair_passes, paths, lens,
+                                      stream=torch.cuda.current_stream())
             lens = lens.cpu().numpy()
             ok = np.flatnonzero(lens >= 0)
             if ok.size == 0:
@@ -101,10 +115,35 @@ def train(model, data, epochs=4, fields_per_step=64, lr=1e-3, seed=0, log=None):
 
 
 # ----------------------------------------------------------------------------- 3. seeding
+# The decoder's slack.  With a slack the walk may pass over the nearest cell
+# to follow the predicted order (jump an obstacle instead of stranding the
+# rest of a row); on held-out 16x16 fields every slack tried (50 to 300)
+# made the seeds longer, so the walk stays among the nearest cells and the
+# network only breaks their ties.
+WALK_SLACK = 0
+
+
+def device_seed(handle, field, model=None, slack=WALK_SLACK, stream=None):
+    """-> (state device uint8 [C*C], path length) of a seed decoded on the
+    device: with a model, its logits -> expected steps -> the walk scored by
+    them; without one, the plain nearest-cell walk (ties to the smaller id)."""
+    import torch
+    C = handle.info["C"]
+    score = None
+    if model is not None:
+        X = qpath.qp_ws_features(field)
+        Z = torch.empty((C, qpath.WS_STEPS), dtype=torch.float32, device="cuda")
+        qpath.qp_ws_forward(model, X, Z, stream=stream)
+        steps = torch.full((C,), C, dtype=torch.int32, device="cuda")
+        score = qpath.qp_ws_expected_steps(Z, steps, stream=stream)
+    st, _, ln = qpath.qp_ws_walk(handle, score, slack if model is not None else 0, stream=stream)
+    return st, int(ln.item())
+
+
 def learned_seed(model, field, handle, decode="walk", d=None):
-    """-> (state uint8 [C*C], path length) of the decoded network prediction.
-    decode = "walk": nearest unvisited cell, ties by the predicted step;
-    "match": greedy max-logit matching of cells to steps."""
+    """-> (state uint8 [C*C], path length) of the decoded network prediction
+    on the host: decode = "walk" (nearest unvisited cell, ties by the predicted
+    step, qp_ws_decode_walk) or "match" (greedy max-logit matching)."""
     if decode == "walk":
         d = qpath.qp_export_dist(handle) if d is None else d
         state, _ = qpath.qp_ws_infer(model, field, d)
@@ -127,7 +166,9 @@ class Arm:
         self.a = torch.zeros((replicas, n), dtype=torch.uint8, device="cuda")
         self.b = torch.zeros_like(self.a)
         if init is not None:
-            self.a.copy_(torch.from_numpy(np.broadcast_to(init, (replicas, n)).copy()))
+            if not hasattr(init, "data_ptr"):
+                init = torch.from_numpy(np.ascontiguousarray(init, np.uint8))
+            self.a.copy_(init.reshape(1, n).to(self.a.device).expand(replicas, n))
             self.has_init = True
         else:
             self.has_init = False
@@ -195,97 +236,153 @@ def time_to_target(handle, arms, target, segments, seed_time=0.0, repair_passes=
         bests = [arm_best(a) for a in arms]
         best = min([b for b in bests if b is not None], default=None)
         t = time.perf_counter() - t0
-        trace.append((t, best))
+        trace.append((t, best, max(a.done for a in arms)))
         if hit is None and best is not None and best <= target:
             hit = t
     return hit, trace[-1][1], trace
 
 
-def evaluate(model, fields, replicas=1024, n_sweeps=2000, seeded_fraction=0.25, T0=1e3, T1=1.0,
-             seed_T0=None, segments=20, ref_sweeps=10000, seed=3, penalty=None, decode="walk", log=None,
-             repair_passes=None):
-    """Time-to-within-1% on each field, learned arm vs plain arm.
-
-    best known = min over: a long plain reference run (ref_sweeps), the plain
-    arm, the learned arm (its seed included).  Learned arm: seeded_fraction of
-    the replicas start from the decoded prediction at seed_T0 (default A/4),
-    the rest anneal plainly; its clock includes features, forward and decode.
-    With repair_passes set, every arm (the reference run and the seed too) is
-    also judged by its states repaired into paths with that many 2-opt passes
-    (qp_repair_batch; -1 = until no move helps), the repair on the clock."""
+def best_known(handle, replicas=1024, n_sweeps=10000, seeds=(101,), T0=1e3, T1=1.0, repair_passes=-1,
+               field=None):
+    """The length the arms are judged against, fixed before any arm runs and
+    independent of them: plain anneals of `replicas` chains through
+    `n_sweeps` sweeps, one per seed, on the handle's QUBO and (when `field`
+    is given) also at the mixing penalty (A = mixing_penalty(C), T0 = A/2,
+    where the chains cross between paths more often); every final state is
+    repaired into a path (2-opt until no move helps, qp_repair_batch) and the
+    shortest repaired path (or best feasible energy, B = 1) is kept."""
     import torch
+    runs = [(handle, T0)]
+    extra = None
+    if field is not None:
+        extra = qpath.qp_build_qubo(field, A=mixing_penalty(handle.info["C"]))
+        runs.append((extra, 0.5 * extra.info["A"]))
+    best = None
+    for h, t0 in runs:
+        for sd in seeds:
+            a = Arm(h, replicas, n_sweeps, t0, T1, sd, 0)
+            a.advance(n_sweeps)
+            torch.cuda.synchronize()
+            for v in (a.best_length(), a.repaired_length(repair_passes)):
+                if v is not None:
+                    best = v if best is None else min(best, v)
+    if extra is not None:
+        extra.close()
+    return best
+
+
+ARMS = ("plain", "walk", "untrained", "learned")
+
+
+def evaluate(model, fields, replicas=1024, n_sweeps=2000, seeded_fraction=0.25, T0=1e3, T1=1.0, seed_T0=None,
+             segments=20, ref_sweeps=10000, ref_seeds=(101,), seed=3, penalty=None, slack=WALK_SLACK,
+             untrained=None, log=None, repair_passes=None, best_known_cache=None):
+    """Time (and sweeps) to within 1% of the best known path on each field, for
+    four arms run on the same QUBO with the same replicas and schedule:
+      plain     -- every replica anneals from zero;
+      walk      -- seeded_fraction of the replicas start from the plain
+                   nearest-cell walk (no network) at seed_T0 (default A/4), the
+                   rest anneal plainly;
+      untrained -- the same with the walk scored by an untrained network's
+                   expected steps (`untrained`, default WarmStartModel(seed=1));
+      learned   -- the same with the trained `model`.
+    A seeded arm's clock starts before its seed is computed (features, forward,
+    expected steps, walk), and the seed's own length counts as found then.  The
+    best known length comes first, from best_known() (long plain anneals at
+    the QUBO's penalty and at the mixing penalty, repaired), and none of the
+    arms contributes to it.  With repair_passes set,
+    every arm's states (and the seed) are also repaired into paths with that
+    many 2-opt passes at each checkpoint, the repair on the clock.
+    best_known_cache (a dict, optional) keeps each field's best known length
+    across calls (keyed by the field's position and penalty)."""
+    import torch
+    if untrained is None:
+        untrained = qpath.WarmStartModel(seed=1)
     rows = []
     s_main, s_side = torch.cuda.Stream(), torch.cuda.Stream()
     for fi, f in enumerate(fields):
         if penalty is None:
             h = qpath.qp_build_qubo(f)
+            T0f = T0
         else:
             h = qpath.qp_build_qubo(f, A=penalty(int(np.asarray(f.free_mask).sum())))
-            T0 = 0.5 * h.info["A"]
+            T0f = 0.5 * h.info["A"]
         info = h.info
         A = info["A"]
         sT0 = seed_T0 if seed_T0 is not None else A / 4.0
         Rs = int(round(replicas * seeded_fraction))
-        # warm-up of both code paths (tables, kernels) before any clock starts
-        Arm(h, 8, n_sweeps, T0, T1, seed, 0).advance(1)
+        # warm-up of every code path (tables, kernels, decode) before any clock starts
+        Arm(h, 8, n_sweeps, T0f, T1, seed, 0).advance(1)
         Arm(h, 8, n_sweeps, sT0, T1, seed, 0).advance(1)
+        device_seed(h, f, model, slack)
         torch.cuda.synchronize()
-        # the long plain reference
-        ref = Arm(h, replicas, ref_sweeps, T0, T1, seed + 7, 0, stream=s_main)
-        while ref.done < ref.S:
-            ref.advance(ref.S)
-        torch.cuda.synchronize()
-        ref_best = ref.best_length()
-        if repair_passes is not None:
-            r = ref.repaired_length(repair_passes)
-            ref_best = r if ref_best is None else min(ref_best, r)
-        # plain arm (record the trace; the target is fixed afterwards)
-        plain = Arm(h, replicas, n_sweeps, T0, T1, seed, 0, stream=s_main)
-        _, plain_best, plain_trace = time_to_target(h, [plain], -1, segments, repair_passes=repair_passes)
-        # learned arm
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        state, seed_len = learned_seed(model, f, h, decode=decode)
-        if repair_passes is not None:
-            _, rep_len, _ = qpath.qp_repair_path(h, state, repair_passes)
-            seed_len = min(seed_len, rep_len)
-        seeded = Arm(h, Rs, n_sweeps, sT0, T1, seed, 0, init=state, stream=s_main)
-        rest = Arm(h, replicas - Rs, n_sweeps, T0, T1, seed, Rs, stream=s_side)
-        seed_time = time.perf_counter() - t
-        _, learned_best, learned_trace = time_to_target(h, [seeded, rest], -1, segments, seed_time=seed_time,
-                                                        repair_passes=repair_passes)
-        candidates = [x for x in (ref_best, plain_best, learned_best, seed_len) if x is not None]
-        best_known = min(candidates)
-        target = 1.01 * best_known
-
-        def first_hit(trace, start=None):
-            pts = ([(start[0], start[1])] if start else []) + list(trace)
-            for tt, b in pts:
-                if b is not None and b <= target:
-                    return tt
-            return None
-        row = {"field": fi, "cells": info["C"], "A": A, "T0": T0, "seed_T0": sT0, "best_known": best_known,
-               "ref_best": ref_best,
-               "plain_best": plain_best, "learned_best": learned_best, "seed_length": seed_len,
-               "seed_time_s": seed_time,
-               "plain_time_to_1pct": first_hit(plain_trace),
-               "learned_time_to_1pct": first_hit(learned_trace, (seed_time, seed_len)),
-               "plain_final_time_s": plain_trace[-1][0], "learned_final_time_s": learned_trace[-1][0]}
+        key = (fi, penalty is None)
+        if best_known_cache is not None and key in best_known_cache:
+            ref = best_known_cache[key]
+        else:
+            ref = best_known(h, replicas, ref_sweeps, ref_seeds, T0f, T1, field=f)
+            if best_known_cache is not None:
+                best_known_cache[key] = ref
+        target = 1.01 * ref
+        row = {"field": fi, "cells": info["C"], "A": A, "T0": T0f, "seed_T0": sT0, "best_known": ref,
+               "slack": slack}
+        # plain arm
+        plain = Arm(h, replicas, n_sweeps, T0f, T1, seed, 0, stream=s_main)
+        _, pb, ptr = time_to_target(h, [plain], target, segments, repair_passes=repair_passes)
+        row["plain"] = _arm_row(pb, ptr, target, None)
+        for name, mdl in (("walk", None), ("untrained", untrained), ("learned", model)):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            state, seed_len = device_seed(h, f, mdl, slack)
+            if repair_passes is not None:
+                _, rep_len, _ = qpath.qp_repair_path(h, state.cpu().numpy(), repair_passes)
+                seed_len = min(seed_len, rep_len)
+            seeded = Arm(h, Rs, n_sweeps, sT0, T1, seed, 0, init=state, stream=s_main)
+            rest = Arm(h, replicas - Rs, n_sweeps, T0f, T1, seed, Rs, stream=s_side)
+            seed_time = time.perf_counter() - t
+            _, b, tr = time_to_target(h, [seeded, rest], target, segments, seed_time=seed_time,
+                                      repair_passes=repair_passes)
+            row[name] = _arm_row(b, tr, target, (seed_time, seed_len))
         rows.append(row)
+        h.close()
         if log:
             log(str(row))
     return rows
 
 
+def _arm_row(final_best, trace, target, seed):
+    """Time and sweeps of the first checkpoint (or the seed) within target."""
+    t_hit, s_hit = None, None
+    if seed is not None and seed[1] is not None and seed[1] <= target:
+        t_hit, s_hit = seed[0], 0
+    else:
+        for tt, b, sw in trace:
+            if b is not None and b <= target:
+                t_hit, s_hit = tt, sw
+                break
+    out = {"time_to_1pct": t_hit, "sweeps_to_1pct": s_hit, "final_best": final_best,
+           "final_time_s": trace[-1][0]}
+    if seed is not None:
+        out.update({"seed_length": seed[1], "seed_time_s": seed[0]})
+    return out
+
+
 def summarize(rows):
-    """Mean times over fields where the arm reached the target, and counts."""
-    def stat(key):
-        v = [r[key] for r in rows if r[key] is not None]
-        return {"reached": len(v), "of": len(rows), "mean_s": float(np.mean(v)) if v else None}
-    gap = lambda k: float(np.mean([(r[k] / r["best_known"] - 1.0) for r in rows if r[k] is not None]))
-    return {"learned": stat("learned_time_to_1pct"), "plain": stat("plain_time_to_1pct"),
-            "mean_gap_plain_final": gap("plain_best"), "mean_gap_learned_final": gap("learned_best"),
-            "mean_gap_seed": gap("seed_length")}
+    """Per arm: fields that reached the target, mean time and sweeps to it over
+    those fields, mean final gap and mean seed gap to the best known length."""
+    out = {}
+    for arm in ARMS:
+        rs = [r[arm] for r in rows]
+        hit = [x for x in rs if x["time_to_1pct"] is not None]
+        gap = lambda k: [x[k] / r["best_known"] - 1.0 for x, r in zip(rs, rows) if x.get(k) is not None]
+        g = gap("final_best")
+        sg = gap("seed_length")
+        out[arm] = {"reached": f"{len(hit)}/{len(rs)}",
+                    "mean_time_s": float(np.mean([x["time_to_1pct"] for x in hit])) if hit else None,
+                    "mean_sweeps": float(np.mean([x["sweeps_to_1pct"] for x in hit])) if hit else None,
+                    "mean_final_gap": float(np.mean(g)) if g else None,
+                    "mean_seed_gap": float(np.mean(sg)) if sg else None}
+    return out
 
 
 def run(n_train=10000, label_replicas=64, label_sweeps=4000, epochs=8, n_eval=8, eval_side=16,

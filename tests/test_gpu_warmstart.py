@@ -1,5 +1,14 @@
-"""The learned warm start end to end: labels from the annealer, training on
-the GPU, seeds for held-out fields, and what it gains over plain annealing."""
+"""The learned warm start end to end: labels from the annealer (final states
+repaired into paths), training on the GPU, seeds decoded on the device for
+held-out fields, and the arms judged against a best known path that is fixed
+before any arm runs.
+
+What the measurements support, and what is asserted: a trained network breaks
+the walk's ties far better than an untrained one (its seeds are shorter), and
+seeding a quarter of the replicas (from the walk alone or with the trained
+network) reaches within 1% of the best known path in fewer sweeps than plain
+annealing.  The trained network does not give shorter seeds than the walk
+without a network (ties to the smaller cell id), so no test claims that."""
 import numpy as np
 import pytest
 
@@ -16,39 +25,50 @@ def trained():
         pytest.skip("no CUDA device")
     qbuild.build()
     fields = inputs.fields_8_16(768, seed=1000)
-    data = warmstart.annealer_labels(fields, replicas=32, n_sweeps=2000)
+    data = warmstart.annealer_labels(fields, replicas=32, n_sweeps=2000, repair_passes=-1)
     assert len(data) >= 700
+    # repaired labels are paths within a few percent of the 100 (C - 1) bound
+    assert np.mean([d[2] / (100 * (len(d[1]) - 1)) for d in data]) < 1.15
     m = qpath.WarmStartModel(seed=1)
     losses = warmstart.train(m, data, epochs=6)
-    assert losses[-1] < losses[0]
+    assert np.mean(losses[-5:]) < np.mean(losses[:5])
     return m
 
 
 def test_seeds_are_feasible_paths_and_training_helps(trained):
     m0 = qpath.WarmStartModel(seed=1)
     ev = inputs.fields_8_16(6, seed=999999, square=16)
-    tr, un = [], []
+    L = {"trained": [], "untrained": [], "walk": []}
     for f in ev:
         h = qpath.qp_build_qubo(f)
         C = h.info["C"]
-        for mm, acc in ((trained, tr), (m0, un)):
-            state, L = warmstart.learned_seed(mm, f, h, decode="walk")
-            x = state.reshape(C, C)
+        for name, mm in (("trained", trained), ("untrained", m0), ("walk", None)):
+            state, length = warmstart.device_seed(h, f, mm)
+            x = state.cpu().numpy().reshape(C, C)
             assert (x.sum(0) == 1).all() and (x.sum(1) == 1).all()
             assert x[0, warmstart.start_cell(f)] == 1
-            acc.append(L)
-        # the matching decode also yields a feasible path
-        state, L = warmstart.learned_seed(trained, f, h, decode="match")
-        assert L is not None and L >= 100 * (C - 1)
-    assert np.mean(tr) < np.mean(un), (tr, un)
+            assert qpath.qp_decode_path(h, x.reshape(-1))[1] == length
+            L[name].append(length)
+        # the host decodes also yield feasible paths
+        for dec in ("walk", "match"):
+            _, length = warmstart.learned_seed(trained, f, h, decode=dec)
+            assert length is not None and length >= 100 * (C - 1)
+    assert np.mean(L["trained"]) < 0.97 * np.mean(L["untrained"]), L
 
 
-def test_learned_warm_start_beats_plain_time_to_one_percent(trained):
-    """On held-out 16x16 fields the learned arm (25% of 1024 replicas seeded)
-    is within 1% of the best known path sooner than plain annealing."""
+def test_seeded_arms_reach_the_best_known_sooner_than_plain(trained):
+    """Judged in sweeps (deterministic for the seeds), with every checkpoint's
+    states repaired into paths: both seeded arms get within 1% of the best
+    known path no later than plain annealing, and on at least one field
+    sooner."""
     ev = inputs.fields_8_16(2, seed=424242, square=16)
-    rows = warmstart.evaluate(trained, ev, replicas=1024, n_sweeps=1000, ref_sweeps=3000, segments=10)
+    rows = warmstart.evaluate(trained, ev, replicas=1024, n_sweeps=1000, ref_sweeps=3000, segments=10,
+                              repair_passes=-1)
+    big = 10 ** 9
+    sw = lambda r, arm: big if r[arm]["sweeps_to_1pct"] is None else r[arm]["sweeps_to_1pct"]
     for r in rows:
-        assert r["learned_time_to_1pct"] is not None
-        assert r["plain_time_to_1pct"] is None or r["learned_time_to_1pct"] < r["plain_time_to_1pct"]
-        assert r["learned_best"] <= r["plain_best"]
+        assert r["best_known"] >= 100 * (r["cells"] - 1)
+        for arm in ("walk", "learned"):
+            assert sw(r, arm) <= sw(r, "plain"), (arm, r)
+    for arm in ("walk", "learned"):
+        assert any(sw(r, arm) < sw(r, "plain") for r in rows), (arm, rows)
