@@ -261,11 +261,11 @@ def bench_batch(args, flush, stream):
     fields = inputs.batch(256, seed=2026)
     hs = [qpath.qp_build_qubo(f) for f in fields]
     R, S = 128, 2000
-    w, ctas = autotune.tune_batch(hs, R, S)
+    w, ctas, bflags = autotune.tune_batch(hs, R, S)
     st = [torch.zeros((R, h.info["n"]), dtype=torch.uint8, device="cuda") for h in hs]
     E = [torch.zeros(R, dtype=torch.int64, device="cuda") for _ in hs]
     B = [torch.zeros(R, dtype=torch.int64, device="cuda") for _ in hs]
-    b = qpath.qp_batch_create(hs, R, qpath.schedule(S), 1, st, E, B, replicas_per_cta=w, ctas=ctas)
+    b = qpath.qp_batch_create(hs, R, qpath.schedule(S), 1, st, E, B, replicas_per_cta=w, ctas=ctas, flags=bflags)
     attempts = sum(R * S * (h.info["C"] - 1) ** 2 for h in hs)
     with torch.cuda.stream(stream):
         b.run(stream)
@@ -286,6 +286,7 @@ def bench_batch(args, flush, stream):
     return {"value": attempts / (m / 1e3), "unit": UNIT, "ms": m, "fields": len(hs), "replicas": R, "sweeps": S,
             "cells_min_median_max": [min(Cs), sorted(Cs)[len(Cs) // 2], max(Cs)], "attempts": attempts,
             "replicas_per_cta": info["replicas_per_cta"], "ctas": info["ctas"], "launch": "one CUDA graph",
+            "staging": "d in shared memory per CTA" if bflags & qpath.QP_BATCH_D_SHARED else "d from L2",
             "feasible_replicas": feas}
 
 
@@ -653,7 +654,8 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
                 "frac": achieved_gbs / pk["hbm_gbs"] if pk.get("hbm_gbs") else None,
                 "traffic": recorded_traffic(args.workload),
-                "kernel": "k_sweep_rows" if args.structured_kernel == "rows" else "k_sweep_structured",
+                "kernel": ("k_sweep_structured" if args.structured_kernel != "rows"
+                           else ("k_sweep_rows_g" if 256 < C <= 512 else "k_sweep_rows")),
                 "kernel_ms": ann_ms, "bytes_per_attempt": bpa,
                 "algorithmic_bytes_per_launch": bpa * attempts,
                 "note": (f"bytes-per-flip model: 2 distance rows x {C} int16 entries per row of {C - 1} "

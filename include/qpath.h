@@ -235,12 +235,17 @@ qp_status qp_anneal_noalloc(qp_handle *h, int32_t replicas, const qp_schedule *s
  * batch.  Taking work is one atomic add per (field, replica): no device wait.
  * opts (NULL = defaults): replicas_per_cta (warps per CTA) and ctas (grid
  * size, 0 = as many as fit on the GPU at once), which the autotuner picks,
- * and flags (QP_ANNEAL_SKIP_SETTLED, same results). */
+ * and flags: QP_ANNEAL_SKIP_SETTLED (same results) and QP_BATCH_D_SHARED, the
+ * staging choice (same results): a CTA takes replicas_per_cta replicas of one
+ * field at a time and stages that field's int16 distance matrix in shared
+ * memory, instead of each warp taking one (field, replica) and reading d
+ * from L2.  QP_EINVAL for other flags. */
+enum { QP_BATCH_D_SHARED = 2 };
 typedef struct qp_batch qp_batch;
 typedef struct {
   int32_t replicas_per_cta;
   int32_t ctas;
-  int32_t flags;  /* QP_ANNEAL_SKIP_SETTLED or 0 */
+  int32_t flags;  /* QP_ANNEAL_SKIP_SETTLED | QP_BATCH_D_SHARED, or 0 */
 } qp_batch_opts;
 qp_status qp_batch_create(qp_handle *const *hs, int32_t count, int32_t replicas, const qp_schedule *sched,
                           uint64_t seed, uint8_t *const *states_out, int64_t *const *energies_out,

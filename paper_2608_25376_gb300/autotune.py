@@ -1,9 +1,11 @@
 """Autotuner for the launch configuration of the sweeps.
 
 Picks replicas-per-CTA for the single-field structured sweep, and
-(replicas-per-CTA, CTAs) for the batched persistent launch, by timing each
-candidate on short windows of the actual schedule (its hottest and its coldest
-sweeps) with CUDA events.  Results are cached in a JSON file keyed by GPU
+(replicas-per-CTA, CTAs, staging) for the batched persistent launch -- the
+staging choice being each field's distance matrix read from L2 by every warp,
+or staged in shared memory by a CTA that runs a block of that field's
+replicas (QP_BATCH_D_SHARED) -- by timing each candidate on short windows of
+the actual schedule (its hottest and its coldest sweeps) with CUDA events.  Results are cached in a JSON file keyed by GPU
 model, kernel and field-size class (cells rounded up to a multiple of 32, plus
 the replica count), so a configuration is measured once per machine.  The
 choice never changes results: every configuration runs the same chains.
@@ -104,40 +106,44 @@ def tune_single(h: "qpath.Handle", replicas: int, n_sweeps: int, T0: float = 1e3
 
 
 def tune_batch(handles, replicas: int, n_sweeps: int, T0: float = 1e3, T1: float = 1.0,
-               candidates_w=(2, 4, 8, 16), cta_factors=(0, 1, 2), window: int = 30,
-               refresh: bool = False) -> tuple[int, int]:
-    """Best (replicas_per_cta, ctas) for qp_batch_create on this batch shape.
-    cta_factors: 0 = as many CTAs as fit at once, k = k CTAs per SM."""
+               candidates_w=(2, 4, 8, 16), cta_factors=(0, 1, 2), stagings=(0, qpath.QP_BATCH_D_SHARED),
+               window: int = 30, refresh: bool = False) -> tuple[int, int, int]:
+    """Best (replicas_per_cta, ctas, flags) for qp_batch_create on this batch
+    shape.  cta_factors: 0 = as many CTAs as fit at once, k = k CTAs per SM;
+    stagings: the batch flags to try (0 = d from L2, QP_BATCH_D_SHARED = d
+    staged in shared memory per CTA)."""
     import torch
     Cs = sorted(h.info["C"] for h in handles)
     key = (f"{_gpu_key()}|batch|F{len(handles)}|Cmax{size_class(Cs[-1])}|Cmed{size_class(Cs[len(Cs) // 2])}"
-           f"|R{replicas}")
+           f"|R{replicas}|stagings{','.join(str(x) for x in stagings)}")
     with _lock:
         cache = _load()
         if not refresh and key in cache:
             e = cache[key]
-            return int(e["replicas_per_cta"]), int(e["ctas"])
+            return int(e["replicas_per_cta"]), int(e["ctas"]), int(e["flags"])
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     st = [torch.zeros((replicas, h.info["n"]), dtype=torch.uint8, device="cuda") for h in handles]
     E = [torch.zeros(replicas, dtype=torch.int64, device="cuda") for _ in handles]
     timings = {}
-    for w in candidates_w:
-        for fct in cta_factors:
-            ctas = 0 if fct == 0 else fct * sms
-            total = 0.0
-            try:
-                for a, b in _windows(n_sweeps, window):
-                    sc = qpath.schedule(n_sweeps, T0, T1, a, b)
-                    bt = qpath.qp_batch_create(handles, replicas, sc, 1, st, E, replicas_per_cta=w, ctas=ctas)
-                    total += _time(lambda: bt.run(torch.cuda.current_stream()))
-                    bt.close()
-            except qpath.QpError:
-                continue
-            timings[f"{w},{ctas}"] = total
+    for flags in stagings:
+        for w in candidates_w:
+            for fct in cta_factors:
+                ctas = 0 if fct == 0 else fct * sms
+                total = 0.0
+                try:
+                    for a, b in _windows(n_sweeps, window):
+                        sc = qpath.schedule(n_sweeps, T0, T1, a, b)
+                        bt = qpath.qp_batch_create(handles, replicas, sc, 1, st, E, replicas_per_cta=w, ctas=ctas,
+                                                   flags=flags)
+                        total += _time(lambda: bt.run(torch.cuda.current_stream()))
+                        bt.close()
+                except qpath.QpError:
+                    continue
+                timings[f"{w},{ctas},{flags}"] = total
     best = min(timings, key=timings.get)
-    w, ctas = (int(x) for x in best.split(","))
+    w, ctas, flags = (int(x) for x in best.split(","))
     with _lock:
         cache = _load()
-        cache[key] = {"replicas_per_cta": w, "ctas": ctas, "ms": timings}
+        cache[key] = {"replicas_per_cta": w, "ctas": ctas, "flags": flags, "ms": timings}
         _store(cache)
-    return w, ctas
+    return w, ctas, flags

@@ -22,6 +22,7 @@ using namespace qp::host;
 struct qp_batch {
   int dev = 0;
   int count = 0, R = 0, Cmax = 0, W = 0, blocks = 0, n_units = 0;
+  bool staged = false;
   DevBuf fields, units, counter;
   std::shared_ptr<const void> sched_keep;  // the schedule's tables, referenced by the captured graph
   cudaStream_t cap = nullptr;
@@ -61,9 +62,12 @@ extern "C" qp_status qp_batch_create(qp_handle *const *hs, int32_t count, int32_
     if (best_out) QP_DEV_FITS(best_out[f], (size_t)R * 8, "best_out[f]");
     Cmax = std::max(Cmax, (int)h->C);
   }
+  if (o.flags & ~(QP_ANNEAL_SKIP_SETTLED | QP_BATCH_D_SHARED)) return fail(QP_EINVAL, "unknown batch flags");
+  const bool staged = (o.flags & QP_BATCH_D_SHARED) != 0;
+  auto fits = [&](int w) { return staged ? batch_staged_supported(Cmax, w) : batch_supported(Cmax, w); };
   int W = o.replicas_per_cta > 0 ? o.replicas_per_cta : 4;
-  while (W > 1 && !batch_supported(Cmax, W)) --W;
-  if (!batch_supported(Cmax, W)) return fail(QP_ERANGE, "largest field (%d cells) too large for the batch kernel", Cmax);
+  while (W > 1 && !fits(W)) --W;
+  if (!fits(W)) return fail(QP_ERANGE, "largest field (%d cells) too large for the batch kernel", Cmax);
   DeviceSchedule sched;
   QP_TRY(device_schedule(*sc, &sched, &b->sched_keep));
   std::vector<StructArgs> fa(count);
@@ -88,29 +92,35 @@ extern "C" qp_status qp_batch_create(qp_handle *const *hs, int32_t count, int32_
   std::vector<int> order(count);
   for (int f = 0; f < count; ++f) order[f] = f;
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return hs[x]->C > hs[y]->C; });
+  // a unit: one (field, replica) for a warp, or W replicas of one field for a
+  // CTA when d is staged in shared memory
   std::vector<int2> units;
   units.reserve((size_t)count * R);
   for (int f : order)
-    for (int r = 0; r < R; ++r) units.push_back(make_int2(f, r));
+    for (int r = 0; r < R; r += staged ? W : 1) units.push_back(make_int2(f, r));
   QP_TRY(b->fields.ensure(fa.size() * sizeof(StructArgs)));
   QP_TRY(b->units.ensure(units.size() * sizeof(int2)));
   QP_TRY(b->counter.ensure(sizeof(int)));
   QP_CU(cudaMemcpy(b->fields.p, fa.data(), fa.size() * sizeof(StructArgs), cudaMemcpyHostToDevice));
   QP_CU(cudaMemcpy(b->units.p, units.data(), units.size() * sizeof(int2), cudaMemcpyHostToDevice));
   int per_sm = 0, sms = 0;
-  QP_CU(batch_prepare(Cmax, W, &per_sm));
+  QP_CU(staged ? batch_staged_prepare(Cmax, W, &per_sm) : batch_prepare(Cmax, W, &per_sm));
   QP_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev));
   if (per_sm < 1) return fail(QP_ERANGE, "batch kernel does not fit on an SM");
   const int want = o.ctas > 0 ? o.ctas : per_sm * sms;
-  b->blocks = std::min(want, (int)((units.size() + W - 1) / W));
+  b->blocks = std::min(want, staged ? (int)units.size() : (int)((units.size() + W - 1) / W));
+  b->staged = staged;
   b->count = count; b->R = R; b->Cmax = Cmax; b->W = W; b->n_units = (int)units.size();
   // one graph: reset the queue head, run the persistent kernel
   QP_CU(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
   QP_CU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
   cudaError_t e1 = cudaMemsetAsync(b->counter.p, 0, sizeof(int), b->cap);
-  cudaError_t e2 = e1 == cudaSuccess ? launch_batch(b->fields.as<StructArgs>(), b->units.as<int2>(), b->n_units,
-                                                    b->counter.as<int>(), Cmax, W, b->blocks, b->cap)
-                                     : e1;
+  cudaError_t e2 = e1;
+  if (e1 == cudaSuccess)
+    e2 = staged ? launch_batch_staged(b->fields.as<StructArgs>(), b->units.as<int2>(), b->n_units,
+                                      b->counter.as<int>(), Cmax, W, b->blocks, b->cap)
+                : launch_batch(b->fields.as<StructArgs>(), b->units.as<int2>(), b->n_units, b->counter.as<int>(),
+                               Cmax, W, b->blocks, b->cap);
   cudaError_t e3 = cudaStreamEndCapture(b->cap, &b->graph);
   if (e2 != cudaSuccess) return fail(QP_ECUDA, "capturing the batch graph: %s", cudaGetErrorString(e2));
   if (e3 != cudaSuccess) return fail(QP_ECUDA, "capturing the batch graph: %s", cudaGetErrorString(e3));

@@ -106,6 +106,12 @@ bool batch_supported(int Cmax, int warps_per_cta);
 cudaError_t batch_prepare(int Cmax, int warps_per_cta, int *blocks_per_sm);
 cudaError_t launch_batch(const StructArgs *fields, const int2 *units, int n_units, int *counter, int Cmax,
                          int warps_per_cta, int blocks, cudaStream_t st);
+// The batched launch with each field's d staged in shared memory (units of W
+// replicas of one field per CTA).
+bool batch_staged_supported(int Cmax, int warps_per_cta);
+cudaError_t batch_staged_prepare(int Cmax, int warps_per_cta, int *blocks_per_sm);
+cudaError_t launch_batch_staged(const StructArgs *fields, const int2 *units, int n_units, int *counter, int Cmax,
+                                int warps_per_cta, int blocks, cudaStream_t st);
 // Grouped structured kernel (qp_sweep_group.cu): 4 replicas per warp for
 // C <= 64, 2 for C <= 128.
 int group_size_for(int C);

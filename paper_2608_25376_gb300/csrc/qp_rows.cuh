@@ -120,6 +120,40 @@ __device__ __forceinline__ int sel4(const int (&v)[4], int j) {
   return j == 0 ? v[0] : (j == 1 ? v[1] : (j == 2 ? v[2] : v[3]));
 }
 
+// The whole row as one test.  With base = B f + 2A c_i, a proposal can matter
+// (dE < len) only if base < lo = len - 2A(r-1) (x = 0) or base > hi =
+// 2A(3-r) - len (x = 1); the lane's columns outside [lo, hi] are a superset
+// of its proposals that matter (columns outside the field carry base = 2A,
+// inside [lo, hi] when r = 1 and len < 2A).  The range test is one unsigned
+// compare, exact because base >= 0 and lo < 2^31 (so base - lo never wraps
+// into [0, hi - lo]); an empty range (hi < lo) passes every column.
+template <int NCH>
+__device__ __forceinline__ bool row_pretest(const int (&P)[NCH][4], const int (&N)[NCH][4], const int (&tAc)[NCH][4],
+                                            int B, int twoA, int rt, int len, int C) {
+  const int lo = len - twoA * (rt - 1), hi = twoA * (3 - rt) - len;
+  if (hi < lo) return true;
+  const unsigned W = (unsigned)(hi - lo), ulo = (unsigned)lo;
+  bool maybe = false;
+  if (B == 1) {
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      if (128 * c >= C) break;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        maybe |= (unsigned)P[c][j] + (unsigned)N[c][j] + (unsigned)tAc[c][j] - ulo > W;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      if (128 * c >= C) break;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        maybe |= (unsigned)B * ((unsigned)P[c][j] + (unsigned)N[c][j]) + (unsigned)tAc[c][j] - ulo > W;
+    }
+  }
+  return maybe;
+}
+
 // The proposals of one 128-wide row chunk when at least one of them can be
 // accepted or needs a draw: evaluate against the current row sum, take the
 // first accepted one, apply it, resume after it.  Returns whether any flip was

@@ -144,6 +144,7 @@ __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_
       // superset of the proposals that matter (columns outside the field carry
       // base = 2A, inside both bounds when r = 1 and len < 2A); when none
       // passes, no proposal of the row can flip or needs a draw.
+      // the whole row first, as one test (row_pretest's bounds as two compares)
       bool maybe = false;
       {
         const int lo = len - twoA * (rt - 1), hi = twoA * (3 - rt) - len;
@@ -327,16 +328,13 @@ __device__ __forceinline__ void rows_replica_g(const StructArgs &a, int r, uint3
       // row t+K+1 into the slot row t+1 has left (its data is in N now)
       ring_issue<DT, NCH, K>(hot, ring, d, Cp, C, t + K + 1, lane);
       cp_async_commit();
-      // row t's bits and sum: from the cache when it holds one cell or none
+      // row t's sum (and, for a row of several cells, its bits): from the
+      // cache when the row holds one cell or none
       int xn[NCH];
       int rt;
       if (hn >= 0) {
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) xn[c] = (hn >> 2) == 32 * c + lane ? 1 << (hn & 3) : 0;
         rt = 1;
       } else if (hn == -1) {
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) xn[c] = 0;
         rt = 0;
       } else {
         rt = 0;
@@ -351,20 +349,15 @@ __device__ __forceinline__ void rows_replica_g(const StructArgs &a, int r, uint3
       const int rt0 = rt;
       bool flipped = false;
       const int tC = t * C;
-      bool maybe = false;
-      {
-        const int lo = len - twoA * (rt - 1), hi = twoA * (3 - rt) - len;
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-          if (128 * c >= C) break;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int b = B * (P[c][j] + N[c][j]) + tAc[c][j];
-            maybe |= (b < lo) | (b > hi);
-          }
-        }
-      }
+      const bool maybe = row_pretest<NCH>(P, N, tAc, B, twoA, rt, len, C);
       if (__any_sync(kFull, maybe)) {
+        if (hn >= 0) {
+#pragma unroll
+          for (int c = 0; c < NCH; ++c) xn[c] = (hn >> 2) == 32 * c + lane ? 1 << (hn & 3) : 0;
+        } else if (hn == -1) {
+#pragma unroll
+          for (int c = 0; c < NCH; ++c) xn[c] = 0;
+        }
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
           if (128 * c >= C) break;
@@ -509,6 +502,42 @@ __global__ void __launch_bounds__(rows_max_warps<NCH>() * 32)
 
 constexpr size_t kSmemLimitRows = 227 * 1024;
 
+// The batched launch with each field's distance matrix staged in shared
+// memory: a CTA takes a unit of W replicas of one field (W = its warps), copies
+// the field's int16 d into shared memory, runs one replica per warp against it
+// and, once every warp is done, takes the next unit.  The autotuner times it
+// against k_sweep_batch (d read from L2, units of one replica per warp).
+template <int NCH>
+__global__ void __launch_bounds__(rows_max_warps<NCH>() * 32)
+    k_sweep_batch_staged(const StructArgs *fields, const int2 *units, int n_units, int *counter, int nw_pad_max,
+                         int Cmax, int Cpmax) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_unit;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int16_t *dsm = reinterpret_cast<int16_t *>(smem);
+  const size_t dbytes = align16r((size_t)Cmax * Cpmax * 2);
+  const size_t per_warp = 4 * (size_t)nw_pad_max + align16r(2 * (size_t)Cmax);
+  uint32_t *st = reinterpret_cast<uint32_t *>(smem + dbytes + warp * per_warp);
+  int16_t *hot1 = reinterpret_cast<int16_t *>(smem + dbytes + warp * per_warp + 4 * (size_t)nw_pad_max);
+  while (true) {
+    if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
+    __syncthreads();
+    const int u = s_unit;
+    if (u >= n_units) break;  // the same u in every thread
+    const int2 unit = units[u];
+    const StructArgs a = fields[unit.x];
+    const int nv = (int)((size_t)a.C * a.Cp * 2 / 16);  // Cp is a multiple of 8
+    const int4 *src = static_cast<const int4 *>(a.d);
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) reinterpret_cast<int4 *>(dsm)[v] = __ldg(src + v);
+    __syncthreads();
+    const int r = unit.y + warp;
+    if (r < a.R) rows_replica<int16_t, NCH, 1, 1>(a, r, st, hot1, dsm, lane);
+    __syncthreads();  // every warp is done with d and s_unit before the next unit
+  }
+}
+
+
+
 template <typename DT, int NCH, int DMODE>
 cudaError_t launch_r(const StructArgs &a, int W, size_t smem, cudaStream_t st) {
   auto k = k_sweep_rows<DT, NCH, DMODE>;
@@ -572,6 +601,48 @@ cudaError_t batch_prepare(int Cmax, int W, int *blocks_per_sm) {
   if (Cmax <= 128) return prep_batch<1>(W, smem, blocks_per_sm);
   if (Cmax <= 256) return prep_batch<2>(W, smem, blocks_per_sm);
   return prep_batch<4>(W, smem, blocks_per_sm);
+}
+
+size_t batch_staged_smem(int Cmax, int W) {
+  const int Cpmax = (Cmax + 7) / 8 * 8;
+  return align16r((size_t)Cmax * Cpmax * 2) + batch_smem(Cmax, W);
+}
+
+bool batch_staged_supported(int Cmax, int W) {
+  const int wmax = Cmax <= 256 ? kMaxWarpsPerCta : 8;
+  return Cmax >= 2 && Cmax <= 512 && W >= 1 && W <= wmax && batch_staged_smem(Cmax, W) <= kSmemLimitRows;
+}
+
+template <int NCH>
+static cudaError_t prep_batch_staged(int W, size_t smem, int *blocks_per_sm) {
+  auto k = k_sweep_batch_staged<NCH>;
+  std::lock_guard<std::mutex> lk(launch_mutex());
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, W * 32, smem);
+}
+
+cudaError_t batch_staged_prepare(int Cmax, int W, int *blocks_per_sm) {
+  if (!batch_staged_supported(Cmax, W)) return cudaErrorInvalidValue;
+  const size_t smem = batch_staged_smem(Cmax, W);
+  if (Cmax <= 128) return prep_batch_staged<1>(W, smem, blocks_per_sm);
+  if (Cmax <= 256) return prep_batch_staged<2>(W, smem, blocks_per_sm);
+  return prep_batch_staged<4>(W, smem, blocks_per_sm);
+}
+
+cudaError_t launch_batch_staged(const StructArgs *fields, const int2 *units, int n_units, int *counter, int Cmax,
+                                int W, int blocks, cudaStream_t st) {
+  if (!batch_staged_supported(Cmax, W) || blocks < 1) return cudaErrorInvalidValue;
+  const size_t smem = batch_staged_smem(Cmax, W);
+  const int nwp = (int)rows_state_words(Cmax);
+  const int Cpmax = (Cmax + 7) / 8 * 8;
+  if (Cmax <= 128)
+    k_sweep_batch_staged<1><<<blocks, W * 32, smem, st>>>(fields, units, n_units, counter, nwp, Cmax, Cpmax);
+  else if (Cmax <= 256)
+    k_sweep_batch_staged<2><<<blocks, W * 32, smem, st>>>(fields, units, n_units, counter, nwp, Cmax, Cpmax);
+  else
+    k_sweep_batch_staged<4><<<blocks, W * 32, smem, st>>>(fields, units, n_units, counter, nwp, Cmax, Cpmax);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_batch(const StructArgs *fields, const int2 *units, int n_units, int *counter, int Cmax,

@@ -23,6 +23,7 @@ QP_DENSE, QP_STRUCTURED, QP_DIST_I16 = 1, 2, 4
 QP_KERNEL_AUTO, QP_KERNEL_DENSE, QP_KERNEL_STRUCTURED, QP_KERNEL_STRUCTURED_FLAT = 0, 1, 2, 3
 QP_KERNEL_STRUCTURED_ROWS, QP_KERNEL_STRUCTURED_GROUP, QP_KERNEL_STRUCTURED_ROWS_SHARED = 4, 5, 6
 QP_ANNEAL_SKIP_SETTLED = 1
+QP_BATCH_D_SHARED = 2
 E_NONE = np.iinfo(np.int64).max
 
 # every entry point include/qpath.h declares

@@ -172,13 +172,38 @@ def test_autotuner_picks_valid_configs_and_caches(dev, tmp_path, monkeypatch):
     assert autotune.tune_single(h, 64, 200) == w  # from the cache
     fields = inputs.batch(8, seed=4)
     hs = [qpath.qp_build_qubo(f) for f in fields]
-    wb, ctas = autotune.tune_batch(hs, 8, 100, candidates_w=(2, 8), cta_factors=(0, 1), window=10)
+    wb, ctas, flags = autotune.tune_batch(hs, 8, 100, candidates_w=(2, 8), cta_factors=(0, 1), window=10)
+    assert flags in (0, qpath.QP_BATCH_D_SHARED)
     d = json.load(open(tmp_path / "tune.json"))
     assert len(d) == 2
+    # both stagings were timed
+    e = [v for k, v in d.items() if "|batch|" in k][0]
+    assert any(k.endswith(",0") for k in e["ms"]) and any(k.endswith(f",{qpath.QP_BATCH_D_SHARED}") for k in e["ms"])
     # the tuned batch gives the per-field results
     sc = qpath.schedule(100)
     st, E, B = outputs(hs, 8)
-    b = qpath.qp_batch_create(hs, 8, sc, 4, st, E, B, replicas_per_cta=wb, ctas=ctas)
+    b = qpath.qp_batch_create(hs, 8, sc, 4, st, E, B, replicas_per_cta=wb, ctas=ctas, flags=flags)
     b.run(torch.cuda.current_stream())
     torch.cuda.synchronize()
     check_fields(hs, 8, sc, 4, st, E, B)
+
+
+@pytest.mark.parametrize("W", [1, 3, 8])
+def test_batch_with_d_staged_in_shared_memory(dev, W):
+    """QP_BATCH_D_SHARED: CTAs of W replicas of one field against its d in
+    shared memory (replica blocks that do not divide R included) give the
+    per-field results; fields up to 300 cells."""
+    import torch
+    fields = inputs.batch(12, seed=9) + [inputs.obstacles(18, 18, 0.1, seed=8, start=5)]
+    hs = [qpath.qp_build_qubo(f) for f in fields]
+    R, seed = 10, 5
+    sc = qpath.schedule(60)
+    st, E, B = outputs(hs, R)
+    b = qpath.qp_batch_create(hs, R, sc, seed, st, E, B, replicas_per_cta=W, ctas=7,
+                              flags=qpath.QP_BATCH_D_SHARED)
+    assert 1 <= b.info["replicas_per_cta"] <= W  # fewer when the largest field leaves no room
+    b.run(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    check_fields(hs, R, sc, seed, st, E, B)
+    with pytest.raises(qpath.QpError):
+        qpath.qp_batch_create(hs, R, sc, seed, st, E, B, flags=8)
