@@ -488,7 +488,13 @@ qp_status launch_structured_auto(qp_handle *h, StructArgs &a, int W, bool allow_
     while (Wg > 1 && !rows_g_supported(h->C, h->d_i16, Wg)) --Wg;
     QP_TRY(h->gstate.ensure((size_t)a.R * rows_g_words(h->C) * 4));
     a.gstate = h->gstate.as<uint32_t>();
-    QP_CU(launch_rows_g(a, h->d_i16, Wg, st, info));
+    QP_TRY(h->rg_aux.ensure((size_t)(2 + a.R) * 4));
+    QP_TRY(h->rg_carry.ensure((size_t)a.R * 16));
+    QP_TRY(h->kernel_err.ensure(4));
+    QP_CU(cudaMemsetAsync(h->rg_aux.p, 0, (size_t)(2 + a.R) * 4, st));
+    int *aux = h->rg_aux.as<int>();
+    QP_CU(launch_rows_g(a, h->d_i16, Wg, aux, aux + 2, h->rg_carry.as<long long>(), h->kernel_err.as<int>(), st,
+                        info));
     return QP_OK;
   }
   if (allow_rows) {
@@ -590,6 +596,9 @@ extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc
       goto launched;
     }
     // replicas per CTA as asked, else chosen for the most resident chains
+    QP_TRY(h->kernel_err.ensure(4));
+    QP_CU(cudaMemsetAsync(h->kernel_err.p, 0, 4, st));
+    err_armed = true;
     QP_TRY(launch_structured_auto(h, a, o.replicas_per_cta, kernel != QP_KERNEL_STRUCTURED_FLAT, st, &info,
                                   kernel == QP_KERNEL_STRUCTURED_ROWS_SHARED));
   } else {
@@ -623,8 +632,9 @@ launched:
     if (err_armed) {
       int32_t err = 0;
       QP_CU(cudaMemcpy(&err, h->kernel_err.p, 4, cudaMemcpyDeviceToHost));
-      if (err) return fail(QP_ETIMEOUT, "a bulk row copy of the dense sweep did not complete; "
-                                        "the affected replicas report energy INT64_MIN");
+      if (err) return fail(QP_ETIMEOUT, "a bounded device wait gave up (a bulk row copy of the dense sweep, or "
+                                        "a chain segment of the row kernel); the affected replicas report "
+                                        "energy INT64_MIN");
     }
   }
   return QP_OK;

@@ -129,6 +129,7 @@ struct qp_handle {
   qp::host::DevBuf frozen_bits, fval_bits;
   std::vector<uint8_t> frozen_host, fval_host;  // generic QUBOs
   // scratch
+  qp::host::DevBuf rg_aux, rg_carry;  // the segmented row kernel: counter, progress flags, carried best/acc
   qp::host::DevBuf gstate, hbuf, in_stage, st_stage, e_stage, b_stage, a_stage, p_stage, l_stage, r_stage;
   qp::host::DevBuf kernel_err;  // int32 flag: a bulk row copy of the dense sweep did not complete
   qp::host::DevBuf t_states[2], t_E, t_paths, t_len, t_stat;  // qp_anneal_timed

@@ -92,11 +92,15 @@ bool rows_supported(int C, bool d_i16, int warps_per_cta);
 int rows_auto_warps(int C, bool d_i16, int R);
 // The row kernel with the spins in global memory (fields of 257..512 cells):
 // words of one replica's row bitsets, support, occupancy choice, launch
-// (a.gstate: R x rows_g_words(C) words).
+// (a.gstate: R x rows_g_words(C) words).  A launch with more chains than fit
+// on the GPU at once runs persistent over (replica, sweep segment) units.
 size_t rows_g_words(int C);
 bool rows_g_supported(int C, bool d_i16, int warps_per_cta);
 int rows_g_auto_warps(int C, bool d_i16, int R);
-cudaError_t launch_rows_g(const StructArgs &a, bool d_i16, int warps_per_cta, cudaStream_t st, LaunchInfo *info);
+// counter (1 int), progress (R ints) and err (1 int) must be zero at launch;
+// carry: 2R int64 the kernel uses between segments of a chain.
+cudaError_t launch_rows_g(const StructArgs &a, bool d_i16, int warps_per_cta, int *counter, int *progress,
+                          long long *carry, int *err, cudaStream_t st, LaunchInfo *info);
 cudaError_t launch_rows(const StructArgs &a, bool d_i16, int warps_per_cta, cudaStream_t st,
                         LaunchInfo *info);
 // Batched persistent launch (qp_sweep_rows.cu): fields[] per field, units[]

@@ -259,17 +259,19 @@ __device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int
 // exactly one, -1 when it holds none, -2 when it holds several), 2A x column
 // sums, the mask of proposable columns, its energy by Eqs. 3-6 and its
 // violation count.
+// keep_bits: the bitsets already hold the state (a later segment of the
+// same chain): only the derived quantities are rebuilt from them.
 template <typename DT, int NCH, int DMODE, bool SG = false>
 __device__ __forceinline__ void rows_init(const StructArgs &a, int r, uint32_t *st, int16_t *hot1, const void *d,
                                           int lane, int (&tAc)[NCH][4], int (&validc)[NCH], long long &E_out,
-                                          int &viol_out) {
+                                          int &viol_out, bool keep_bits = false) {
   const int C = a.C, Cp = a.Cp, s0 = a.start, A = a.A, B = a.B;
   const int twoA = 2 * A;
   const int Cw = (C + 31) >> 5;
   const int n = C * C;
   // ---- initial state: given or all zero; row 0 and column s clamped (x_{0,s} = 1)
   const uint8_t *init = a.init ? a.init + (size_t)r * n : nullptr;
-  for (int e = lane; e < C * Cw; e += 32) {
+  for (int e = keep_bits ? C * Cw : lane; e < C * Cw; e += 32) {
     const int t = e / Cw, w = e - t * Cw;
     uint32_t word = 0;
     if (t == 0) {

@@ -266,9 +266,15 @@ __device__ __forceinline__ void ring_issue(const int16_t *hot, DT *ring, const v
   }
 }
 
+// Sweeps [sb, se) of replica r.  fresh: the state comes from a.init (or zero);
+// else it is already in the bitsets (a later segment of the chain) and only
+// the cache, the column sums, E and the violation count are rebuilt from it
+// (exactly: E is a function of the state).  best and acc carry the running
+// best energy and accept count in and out; `last` writes the outputs.
 template <typename DT, int NCH, int K>
 __device__ __forceinline__ void rows_replica_g(const StructArgs &a, int r, uint32_t *st, int16_t *hot, DT *ring,
-                                               int lane) {
+                                               int lane, int sb, int se, bool fresh, bool last, long long &best,
+                                               long long &acc) {
   static_assert(K >= 3, "the ring holds rows t+2 .. t+K+1");
   const int C = a.C, Cp = a.Cp, s0 = a.start, A = a.A, B = a.B;
   const int twoA = 2 * A;
@@ -281,13 +287,12 @@ __device__ __forceinline__ void rows_replica_g(const StructArgs &a, int r, uint3
   int validc[NCH];
   long long E;
   int viol;
-  rows_init<DT, NCH, 0, true>(a, r, st, hot, d, lane, tAc, validc, E, viol);
-  long long best = LLONG_MAX, acc = 0;
+  rows_init<DT, NCH, 0, true>(a, r, st, hot, d, lane, tAc, validc, E, viol, !fresh);
 
   const int lev = a.level ? __ldg(a.level + r) : -1;
   bool settled = false;
   int settled_len = 0;
-  for (int s = a.sweep_begin; s < a.sweep_end; ++s) {
+  for (int s = sb; s < se; ++s) {
     const int ts = lev >= 0 ? lev : s;
     const uint32_t *thr = a.thr + a.thr_off[ts];
     const int len = a.thr_len[ts];
@@ -410,6 +415,7 @@ __device__ __forceinline__ void rows_replica_g(const StructArgs &a, int r, uint3
     settled_len = len;
   }
 
+  if (!last) return;
   uint8_t *out = a.states_out + (size_t)r * n;
   for (int e = lane; e < n; e += 32) {
     const int t = e / C, i = e - t * C;
@@ -425,17 +431,73 @@ __device__ __forceinline__ void rows_replica_g(const StructArgs &a, int r, uint3
 constexpr int kRowsGMaxWarps = 12;  // 384 threads: at most 170 registers per thread
 constexpr int kRowsGRing = 8;
 
+// Persistent over (replica, segment) units: the sweeps are cut into G
+// segments and a warp takes units from one counter, segment-major, so the
+// chains' last segments, not whole chains, make up the tail of the launch.
+// The state between segments is the replica's bitsets (global memory) plus
+// its running best energy and accept count (carry[2r], carry[2r+1]).  A
+// segment g > 0 of replica r starts once progress[r] == g: a bounded wait on
+// a flag another running warp sets (units are handed out in order, so the
+// unit it waits for was taken earlier and is running or done); a wait that
+// gives up marks the replica's energy INT64_MIN and sets *err.
+constexpr long long kSegmentWaitCycles = 20000000000LL;  // ~10 s at 2 GHz (a unit takes under 1 s)
+
 template <typename DT, int NCH>
-__global__ void __launch_bounds__(kRowsGMaxWarps * 32) k_sweep_rows_g(const StructArgs a) {
+__global__ void __launch_bounds__(kRowsGMaxWarps * 32)
+    k_sweep_rows_g(const StructArgs a, int G, int *counter, int *progress, long long *carry, int *err) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const size_t hot_bytes = align16r(2 * (size_t)a.C);
   const size_t per_warp = hot_bytes + (size_t)kRowsGRing * a.Cp * sizeof(DT);
   int16_t *hot = reinterpret_cast<int16_t *>(smem + warp * per_warp);
   DT *ring = reinterpret_cast<DT *>(smem + warp * per_warp + hot_bytes);
-  const int r = blockIdx.x * W + warp;
-  if (r >= a.R) return;
-  rows_replica_g<DT, NCH, kRowsGRing>(a, r, a.gstate + (size_t)r * a.nw_pad, hot, ring, lane);
+  const int total = a.R * G;
+  const int nsw = a.sweep_end - a.sweep_begin;
+  const int seg = (nsw + G - 1) / G;
+  while (true) {
+    int u = 0;
+    if (lane == 0) u = atomicAdd(counter, 1);
+    u = __shfl_sync(kFull, u, 0);
+    if (u >= total) break;
+    const int g = u / a.R, r = u - g * a.R;
+    const int sb = a.sweep_begin + min(nsw, g * seg), se = a.sweep_begin + min(nsw, (g + 1) * seg);
+    if (g > 0) {
+      int ok = 1;
+      if (lane == 0) {
+        const long long t0 = clock64();
+        while (true) {
+          int v;
+          asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(progress + r) : "memory");
+          if (v >= g) break;
+          if (clock64() - t0 > kSegmentWaitCycles) { ok = 0; break; }
+          __nanosleep(256);
+        }
+      }
+      ok = __shfl_sync(kFull, ok, 0);
+      if (!ok) {
+        if (lane == 0) {
+          atomicExch(err, 1);
+          a.E_out[r] = LLONG_MIN;
+        }
+        return;  // no copy is in flight between segments
+      }
+    }
+    long long best = LLONG_MAX, acc = 0;
+    if (g > 0) {
+      best = __ldcg(carry + 2 * (size_t)r);
+      acc = __ldcg(carry + 2 * (size_t)r + 1);
+    }
+    const bool last = g == G - 1;
+    rows_replica_g<DT, NCH, kRowsGRing>(a, r, a.gstate + (size_t)r * a.nw_pad, hot, ring, lane, sb, se, g == 0, last,
+                                        best, acc);
+    __syncwarp();
+    if (!last && lane == 0) {
+      carry[2 * (size_t)r] = best;
+      carry[2 * (size_t)r + 1] = acc;
+      __threadfence();  // the bitsets (atomics in L2), best and acc before the flag
+      asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(progress + r), "r"(g + 1) : "memory");
+    }
+  }
 }
 
 // Widest rows (NCH = 4) keep three 16-register fields per lane: they get up to
@@ -765,27 +827,41 @@ int rows_g_auto_warps(int C, bool d_i16, int R) {
   return best_w;
 }
 
-cudaError_t launch_rows_g(const StructArgs &a_in, bool d_i16, int W, cudaStream_t st, LaunchInfo *info) {
+cudaError_t launch_rows_g(const StructArgs &a_in, bool d_i16, int W, int *counter, int *progress, long long *carry,
+                          int *err, cudaStream_t st, LaunchInfo *info) {
   StructArgs a = a_in;
-  if (!rows_g_supported(a.C, d_i16, W) || a.gstate == nullptr) return cudaErrorInvalidValue;
+  if (!rows_g_supported(a.C, d_i16, W) || a.gstate == nullptr || !counter || !progress || !carry || !err)
+    return cudaErrorInvalidValue;
   a.nw_pad = (int32_t)rows_g_words(a.C);
   const size_t smem = rows_g_smem(a.C, d_i16, W);
+  int dev = 0, sms = 0, bps = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = d_i16 ? occ_g<int16_t>(W, smem, &bps) : occ_g<int32_t>(W, smem, &bps);
+  if (e != cudaSuccess) return e;
+  if (bps < 1) return cudaErrorInvalidConfiguration;
+  // more chains than fit at once: cut the sweeps into segments of ~500 so the
+  // launch ends on short units instead of a partial wave of whole chains
+  const long long capacity = (long long)bps * sms * W;
+  const int nsw = a.sweep_end - a.sweep_begin;
+  const int G = (a.R > capacity && nsw >= 1000) ? std::min(64, nsw / 500) : 1;
+  const long long warps_needed = (long long)a.R * G;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>((long long)bps * sms, (warps_needed + W - 1) / W));
   if (info) {
     info->warps_per_cta = W;
-    info->blocks = (a.R + W - 1) / W;
+    info->blocks = blocks;
     info->smem = smem;
-    info->variant = "rows,spins:global,d:L2 ring";
+    info->variant = G > 1 ? "rows,spins:global,d:L2 ring,segments" : "rows,spins:global,d:L2 ring";
   }
   std::lock_guard<std::mutex> lk(launch_mutex());
-  cudaError_t e;
   if (d_i16) {
     auto k = k_sweep_rows_g<int16_t, 4>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) k<<<(a.R + W - 1) / W, W * 32, smem, st>>>(a);
+    if (e == cudaSuccess) k<<<blocks, W * 32, smem, st>>>(a, G, counter, progress, carry, err);
   } else {
     auto k = k_sweep_rows_g<int32_t, 4>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) k<<<(a.R + W - 1) / W, W * 32, smem, st>>>(a);
+    if (e == cudaSuccess) k<<<blocks, W * 32, smem, st>>>(a, G, counter, progress, carry, err);
   }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
