@@ -211,11 +211,17 @@ __device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int
           uw[j] = (j < 4 - delta) ? word_of(u0, wsel) : word_of(u1, wsel);
         }
       }
+      // dE >= dq gives thr[dE] <= thr[dq] = Q, so u >= Q rejects outright: the
+      // proposals still open after that test (branch-free), then their exact
+      // tests, which few proposals reach
+      int open = 0;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        // dE >= dq gives thr[dE] <= thr[dq] = Q, so u >= Q rejects outright
-        if (((need >> j) & 1) && (dE[j] < dq || uw[j] < Q) && accept_draw(uw[j], dE[j], cT, thr, len))
-          accm |= 1 << j;
+      for (int j = 0; j < 4; ++j) open |= (int)((dE[j] < dq) | (uw[j] < Q)) << j;
+      open &= need;
+      if (open) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (((open >> j) & 1) && accept_draw(uw[j], dE[j], cT, thr, len)) accm |= 1 << j;
       }
     }
     const uint32_t bal = __ballot_sync(kFull, accm);
