@@ -201,15 +201,14 @@ __device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int
         u1 = philox4x32_10(make_uint4(b0 + 1, (uint32_t)s, rg, kRngTag), key0, key1);
         h1 = true;
       }
+      // the lane's four draws: words delta..delta+3 of the blocks (u0, u1); delta
+      // is the same for the whole row, so the branch is uniform
       uint32_t uw[4];
-      if (delta == 0) {  // the lane's four proposals are exactly one counter block
-        uw[0] = u0.x; uw[1] = u0.y; uw[2] = u0.z; uw[3] = u0.w;
-      } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int wsel = (delta + j) & 3;
-          uw[j] = (j < 4 - delta) ? word_of(u0, wsel) : word_of(u1, wsel);
-        }
+      switch (delta) {
+        case 0: uw[0] = u0.x; uw[1] = u0.y; uw[2] = u0.z; uw[3] = u0.w; break;
+        case 1: uw[0] = u0.y; uw[1] = u0.z; uw[2] = u0.w; uw[3] = u1.x; break;
+        case 2: uw[0] = u0.z; uw[1] = u0.w; uw[2] = u1.x; uw[3] = u1.y; break;
+        default: uw[0] = u0.w; uw[1] = u1.x; uw[2] = u1.y; uw[3] = u1.z; break;
       }
       // dE >= dq gives thr[dE] <= thr[dq] = Q, so u >= Q rejects outright: the
       // proposals still open after that test (branch-free), then their exact
