@@ -345,7 +345,7 @@ def bench_replica_exchange(f, flush, stream):
     pt = qpath.pt_schedule(M, 2.0, 1000.0, I, rounds)
 
     def timed(fn):
-        flush.fill_(3)
+        flush_l2(flush, stream, 3)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         fn()
@@ -422,7 +422,7 @@ def bench_repair(h, states, R, flush, stream):
     qpath.qp_repair_batch(h, R, states, -1, paths, lens, stat, stream=stream)
     ts = []
     for k in range(3):
-        flush.fill_(k)
+        flush_l2(flush, stream, k)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         qpath.qp_repair_batch(h, R, states, -1, paths, lens, stat, stream=stream)
@@ -466,6 +466,15 @@ def cpu_other_rows(P, repair_states, with_pt):
     return out
 
 
+def flush_l2(flush, stream, k):
+    """Evict L2 by a write larger than it, on `stream`, so the flush is done
+    before the events recorded after it (a flush on another stream would
+    overlap the timed kernel)."""
+    import torch
+    with torch.cuda.stream(stream):
+        flush.fill_(k)
+
+
 def timed_anneal(h, R, sc, seed, flush, stream, runs=2, warm=True, **kw):
     """CUDA-event times (ms, on `stream`) of `runs` calls of qp_anneal_ex after
     an optional warm-up call; L2 flushed before each."""
@@ -482,7 +491,7 @@ def timed_anneal(h, R, sc, seed, flush, stream, runs=2, warm=True, **kw):
         qpath.qp_anneal_ex(h, R, sc, seed, None, st, E, B, accepts_out=acc, stream=stream, **kw)
     ms = []
     for k in range(runs):
-        flush.fill_(k)
+        flush_l2(flush, stream, k)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         qpath.qp_anneal_ex(h, R, sc, seed, None, st, E, B, accepts_out=acc, stream=stream, **kw)

@@ -266,6 +266,140 @@ __device__ __forceinline__ void ring_issue(const int16_t *hot, DT *ring, const v
   }
 }
 
+// The parameters of the whole-row test that stay fixed through a sweep.
+struct RowTest {
+  int B, twoA, len, C;
+};
+
+// X0 <- X1 <- X2 <- X3 <- X0
+template <int NCH>
+__device__ __forceinline__ void rotate_fields(int (&X0)[NCH][4], int (&X1)[NCH][4], int (&X2)[NCH][4],
+                                              int (&X3)[NCH][4]) {
+#pragma unroll
+  for (int c = 0; c < NCH; ++c)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int v = X0[c][j];
+      X0[c][j] = X1[c][j];
+      X1[c][j] = X2[c][j];
+      X2[c][j] = X3[c][j];
+      X3[c][j] = v;
+    }
+}
+
+template <int NCH>
+__device__ __forceinline__ void swap_fields(int (&X)[NCH][4], int (&Y)[NCH][4]) {
+#pragma unroll
+  for (int c = 0; c < NCH; ++c)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int v = X[c][j];
+      X[c][j] = Y[c][j];
+      Y[c][j] = v;
+    }
+}
+
+// The front half of row t, the whole work of a row that cannot flip: F_{t+2}
+// into Fl (from its ring slot, or from the row's bits when it does not hold
+// exactly one cell), the ring copy of row t+K+1, row t's sum rt (and, for a
+// row of several cells, its four-bit groups xn), and the whole-row test
+// against P = F_{t-1}, N = F_{t+1}.  hn: the single-cell cache of row t.
+template <typename DT, int NCH, int K>
+__device__ __forceinline__ bool rows_g_front(const uint32_t *st, const int16_t *hot, DT *ring, const void *d, int Cp,
+                                             int C, int Cw, int lane, int t, int hn, const int (&P)[NCH][4],
+                                             const int (&N)[NCH][4], int (&Fl)[NCH][4], const int (&tAc)[NCH][4],
+                                             const RowTest &rtst, int &rt, int (&xn)[NCH]) {
+  if (t + 2 < C) {
+    cp_async_wait<K - 2>();  // row t+2's copy (issued K-1 rows ago) has landed
+    const int h2 = hot[t + 2];
+    if (h2 >= 0) set_drow<DT, NCH, 1>(ring + (size_t)((t + 2) % K) * Cp, Cp, C, 0, lane, Fl);
+    else field_g<DT, NCH>(st, Cw, h2, t + 2, d, Cp, C, lane, Fl);
+  } else {
+    zero<NCH>(Fl);  // past the last row
+  }
+  // row t+K+1 into the slot row t+1 has left (its data is in N now)
+  ring_issue<DT, NCH, K>(hot, ring, d, Cp, C, t + K + 1, lane);
+  cp_async_commit();
+  // row t's sum (and, for a row of several cells, its bits): from the cache
+  // when the row holds one cell or none
+  if (hn >= 0) {
+    rt = 1;
+  } else if (hn == -1) {
+    rt = 0;
+  } else {
+    const uint32_t *row = st + (size_t)t * Cw;
+    rt = 0;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      xn[c] = 128 * c + 4 * lane < C ? (int)((__ldcg(row + 4 * c + (lane >> 3)) >> (4 * (lane & 7))) & 0xFu) : 0;
+      rt += __popc(xn[c]);
+    }
+    rt = __reduce_add_sync(kFull, rt);
+  }
+  return __any_sync(kFull, row_pretest<NCH>(P, N, tAc, rtst.B, rtst.twoA, rt, rtst.len, rtst.C));
+}
+
+// The back half of a row that may flip (P = F_{t-1}, Cu = F_t, N = F_{t+1}):
+// every chunk with a proposal that can be accepted or needs a draw, the
+// violation count, and the row's cache entry when a flip changed it.
+// Returns whether any proposal had dE < len.
+template <typename DT, int NCH>
+__device__ __forceinline__ bool rows_g_flip(const StructArgs &a, uint32_t *st, int16_t *hot, const void *d, int Cp,
+                                            int C, int Cw, int lane, int t, int s, int hn, int rt, int (&xn)[NCH],
+                                            const int (&P)[NCH][4], int (&Cu)[NCH][4], const int (&N)[NCH][4],
+                                            int (&tAc)[NCH][4], const int (&validc)[NCH], long long &E,
+                                            long long &acc, int &viol, int twoA, int len, unsigned lenm1, float cT,
+                                            int dq, uint32_t Q, const uint32_t *thr, uint32_t rg) {
+  uint32_t *row = st + (size_t)t * Cw;
+  const int rt0 = rt;
+  const int B = a.B;
+  bool flipped = false, any_hit = false;
+  const int tC = t * C;
+  if (hn >= 0) {
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) xn[c] = (hn >> 2) == 32 * c + lane ? 1 << (hn & 3) : 0;
+  } else if (hn == -1) {
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) xn[c] = 0;
+  }
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    if (128 * c >= C) break;
+    int base[4], de[4];
+    unsigned hit = 0;
+    {
+      const int k0 = twoA * (rt - 1), k1 = twoA * (3 - rt);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        base[j] = B * (P[c][j] + N[c][j]) + tAc[c][j];
+        de[j] = ((xn[c] >> j) & 1) ? k1 - base[j] : base[j] + k0;
+        hit |= (unsigned)(de[j] < len) << j;
+      }
+    }
+    if (__any_sync(kFull, hit & validc[c])) {
+      any_hit = true;
+      flipped |= row_chunk<DT, NCH, 0, true>(c, t, s, tC, base, de, xn[c], validc[c], tAc[c], rt, Cu, row, E, acc,
+                                             viol, d, Cp, C, lane, twoA, len, lenm1, cT, dq, Q, thr, rg, a.key0,
+                                             a.key1);
+    }
+  }
+  viol += (rt != 1) - (rt0 != 1);
+  if (flipped) {
+    int code = rt == 0 ? -1 : -2;
+    if (rt == 1) {
+      int mine = -1;
+#pragma unroll
+      for (int c = 0; c < NCH; ++c)
+        if (xn[c]) mine = 128 * c + 4 * lane + __ffs(xn[c]) - 1;
+      const unsigned bal = __ballot_sync(kFull, mine >= 0);
+      code = __shfl_sync(kFull, mine, __ffs(bal) - 1);
+    }
+    if (lane == 0) hot[t] = (int16_t)code;
+    __syncwarp();
+  }
+  return any_hit;
+}
+
 // Sweeps [sb, se) of replica r.  fresh: the state comes from a.init (or zero);
 // else it is already in the bitsets (a later segment of the chain) and only
 // the cache, the column sums, E and the violation count are rebuilt from it
@@ -302,111 +436,69 @@ __device__ __forceinline__ void rows_replica_g(const StructArgs &a, int r, uint3
     const float cT = a.thr_c[ts];
     const int dq = len > 1 ? min(len - 1, max(1, (int)fminf(8.0f / cT, 1.0e9f))) : 1;
     const uint32_t Q = len > 1 ? __ldg(a.thr + a.thr_off[ts] + dq) : 0u;
-    // P, Cu, N: the fields of rows t-1, t, t+1; Nn: row t+2's, read from the
-    // ring one row ahead
-    int P[NCH][4], Cu[NCH][4], N[NCH][4], Nn[NCH][4];
-    zero<NCH>(P);
-    add_drow<DT, NCH, 0>(d, Cp, C, s0, lane, 1, P);  // row 0 holds only the start cell
-    field_g<DT, NCH>(st, Cw, hot[1], 1, d, Cp, C, lane, Cu);
-    if (C > 2) field_g<DT, NCH>(st, Cw, hot[2], 2, d, Cp, C, lane, Nn);
-    else zero<NCH>(Nn);
+    // X0..X3 hold the fields of rows t-1, t, t+1 and t+2 (the last read from
+    // the ring) in roles that rotate by one per row
+    int X0[NCH][4], X1[NCH][4], X2[NCH][4], X3[NCH][4];
+    zero<NCH>(X0);
+    add_drow<DT, NCH, 0>(d, Cp, C, s0, lane, 1, X0);  // row 0 holds only the start cell
+    field_g<DT, NCH>(st, Cw, hot[1], 1, d, Cp, C, lane, X1);
+    if (C > 2) field_g<DT, NCH>(st, Cw, hot[2], 2, d, Cp, C, lane, X2);
+    else zero<NCH>(X2);
     // the ring holds rows t+2 .. t+K+1 while row t runs; rows 3 .. K+1 first
     for (int u = 3; u <= K + 1; ++u) {
       ring_issue<DT, NCH, K>(hot, ring, d, Cp, C, u, lane);
       cp_async_commit();
     }
+    int t = 1;
     int hn = hot[1];
-    for (int t = 1; t < C; ++t) {
-      uint32_t *row = st + (size_t)t * Cw;
-#pragma unroll
-      for (int c = 0; c < NCH; ++c)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) N[c][j] = Nn[c][j];
-      if (t + 2 < C) {
-        cp_async_wait<K - 2>();  // row t+2's copy (issued K-1 rows ago) has landed
-        const int h2 = hot[t + 2];
-        if (h2 >= 0) set_drow<DT, NCH, 1>(ring + (size_t)((t + 2) % K) * Cp, Cp, C, 0, lane, Nn);
-        else field_g<DT, NCH>(st, Cw, h2, t + 2, d, Cp, C, lane, Nn);
+    const RowTest rtst{B, twoA, len, C};
+    while (true) {
+      // Rows the whole-row test clears change nothing, so four of them run
+      // with the fields' roles rotated, (P, N, F_{t+2}) = (X0, X2, X3), (X1,
+      // X3, X0), (X2, X0, X1), (X3, X1, X2), and move no register; a row that
+      // may flip leaves the cycle with `from` = its place in it, and its
+      // fields are rotated into P = X0, Cu = X1, N = X2, F_{t+2} = X3.
+      int rt, xn[NCH], from;
+      if (rows_g_front<DT, NCH, K>(st, hot, ring, d, Cp, C, Cw, lane, t, hn, X0, X2, X3, tAc, rtst, rt, xn)) {
+        from = 0;
       } else {
-        zero<NCH>(Nn);  // past the last row
-      }
-      // row t+K+1 into the slot row t+1 has left (its data is in N now)
-      ring_issue<DT, NCH, K>(hot, ring, d, Cp, C, t + K + 1, lane);
-      cp_async_commit();
-      // row t's sum (and, for a row of several cells, its bits): from the
-      // cache when the row holds one cell or none
-      int xn[NCH];
-      int rt;
-      if (hn >= 0) {
-        rt = 1;
-      } else if (hn == -1) {
-        rt = 0;
-      } else {
-        rt = 0;
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-          xn[c] = 128 * c + 4 * lane < C ? (int)((__ldcg(row + 4 * c + (lane >> 3)) >> (4 * (lane & 7))) & 0xFu) : 0;
-          rt += __popc(xn[c]);
-        }
-        rt = __reduce_add_sync(kFull, rt);
-      }
-      const int hn_next = t + 1 < C ? hot[t + 1] : -1;
-      const int rt0 = rt;
-      bool flipped = false;
-      const int tC = t * C;
-      const bool maybe = row_pretest<NCH>(P, N, tAc, B, twoA, rt, len, C);
-      if (__any_sync(kFull, maybe)) {
-        if (hn >= 0) {
-#pragma unroll
-          for (int c = 0; c < NCH; ++c) xn[c] = (hn >> 2) == 32 * c + lane ? 1 << (hn & 3) : 0;
-        } else if (hn == -1) {
-#pragma unroll
-          for (int c = 0; c < NCH; ++c) xn[c] = 0;
-        }
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-          if (128 * c >= C) break;
-          int base[4], de[4];
-          unsigned hit = 0;
-          {
-            const int k0 = twoA * (rt - 1), k1 = twoA * (3 - rt);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              base[j] = B * (P[c][j] + N[c][j]) + tAc[c][j];
-              de[j] = ((xn[c] >> j) & 1) ? k1 - base[j] : base[j] + k0;
-              hit |= (unsigned)(de[j] < len) << j;
+        if (++t >= C) break;
+        hn = hot[t];
+        if (rows_g_front<DT, NCH, K>(st, hot, ring, d, Cp, C, Cw, lane, t, hn, X1, X3, X0, tAc, rtst, rt, xn)) {
+          from = 1;
+        } else {
+          if (++t >= C) break;
+          hn = hot[t];
+          if (rows_g_front<DT, NCH, K>(st, hot, ring, d, Cp, C, Cw, lane, t, hn, X2, X0, X1, tAc, rtst, rt, xn)) {
+            from = 2;
+          } else {
+            if (++t >= C) break;
+            hn = hot[t];
+            if (rows_g_front<DT, NCH, K>(st, hot, ring, d, Cp, C, Cw, lane, t, hn, X3, X1, X2, tAc, rtst, rt, xn)) {
+              from = 3;
+            } else {
+              if (++t >= C) break;
+              hn = hot[t];
+              continue;
             }
           }
-          if (__any_sync(kFull, hit & validc[c])) {
-            any_hit = true;
-            flipped |= row_chunk<DT, NCH, 0, true>(c, t, s, tC, base, de, xn[c], validc[c], tAc[c], rt, Cu, row,
-                                                   E, acc, viol, d, Cp, C, lane, twoA, len, lenm1, cT, dq, Q, thr,
-                                                   rg, a.key0, a.key1);
-          }
         }
       }
-      viol += (rt != 1) - (rt0 != 1);
-      if (flipped) {
-        int code = rt == 0 ? -1 : -2;
-        if (rt == 1) {
-          int mine = -1;
-#pragma unroll
-          for (int c = 0; c < NCH; ++c)
-            if (xn[c]) mine = 128 * c + 4 * lane + __ffs(xn[c]) - 1;
-          const unsigned bal = __ballot_sync(kFull, mine >= 0);
-          code = __shfl_sync(kFull, mine, __ffs(bal) - 1);
-        }
-        if (lane == 0) hot[t] = (int16_t)code;
-        __syncwarp();
-      }
+      if (from == 1) rotate_fields<NCH>(X0, X1, X2, X3);
+      else if (from == 2) { swap_fields<NCH>(X0, X2); swap_fields<NCH>(X1, X3); }
+      else if (from == 3) rotate_fields<NCH>(X3, X2, X1, X0);
+      any_hit |= rows_g_flip<DT, NCH>(a, st, hot, d, Cp, C, Cw, lane, t, s, hn, rt, xn, X0, X1, X2, tAc, validc, E,
+                                      acc, viol, twoA, len, lenm1, cT, dq, Q, thr, rg);
 #pragma unroll
       for (int c = 0; c < NCH; ++c)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          P[c][j] = Cu[c][j];
-          Cu[c][j] = N[c][j];
+          X0[c][j] = X1[c][j];
+          X1[c][j] = X2[c][j];
+          X2[c][j] = X3[c][j];
         }
-      hn = hn_next;
+      if (++t >= C) break;
+      hn = hot[t];
     }
     cp_async_wait<0>();  // the next sweep refills every slot
     __syncwarp();
