@@ -257,12 +257,17 @@ __device__ __forceinline__ void ring_issue(const int16_t *hot, DT *ring, const v
   if (u >= C) return;
   const int h = hot[u];
   if (h < 0) return;
-  DT *slot = ring + (size_t)(u % K) * Cp;
-  const DT *src = static_cast<const DT *>(d) + (size_t)QP_IX(h, C, 2) * Cp;
+  // the whole padded row (Cp entries, Cp a multiple of 8) in 16-byte pieces
+  // spread over the lanes: a lane's columns come from other lanes' copies,
+  // so a reader waits for its own copies and then syncs the warp
+  char *slot = reinterpret_cast<char *>(ring + (size_t)((unsigned)u % K) * Cp);
+  const char *src = reinterpret_cast<const char *>(static_cast<const DT *>(d) + (size_t)QP_IX(h, C, 2) * Cp);
+  const int pieces = Cp * (int)sizeof(DT) / 16;
+  constexpr int kIter = (128 * NCH * (int)sizeof(DT) / 16 + 31) / 32;
 #pragma unroll
-  for (int c = 0; c < NCH; ++c) {
-    const int i = 128 * c + 4 * lane;
-    if (i < C) cp_async<4 * (int)sizeof(DT)>(slot + i, src + i);
+  for (int k = 0; k < kIter; ++k) {
+    const int pc = lane + 32 * k;
+    if (pc < pieces) cp_async<16>(slot + 16 * pc, src + 16 * pc);
   }
 }
 
@@ -310,9 +315,10 @@ __device__ __forceinline__ bool rows_g_front(const uint32_t *st, const int16_t *
                                              const int (&N)[NCH][4], int (&Fl)[NCH][4], const int (&tAc)[NCH][4],
                                              const RowTest &rtst, int &rt, int (&xn)[NCH]) {
   if (t + 2 < C) {
-    cp_async_wait<K - 2>();  // row t+2's copy (issued K-1 rows ago) has landed
+    cp_async_wait<K - 2>();  // this lane's copies of row t+2 (issued K-1 rows ago) have landed
+    __syncwarp();            // ... and every other lane's
     const int h2 = hot[t + 2];
-    if (h2 >= 0) set_drow<DT, NCH, 1>(ring + (size_t)((t + 2) % K) * Cp, Cp, C, 0, lane, Fl);
+    if (h2 >= 0) set_drow<DT, NCH, 1>(ring + (size_t)((unsigned)(t + 2) % K) * Cp, Cp, C, 0, lane, Fl);
     else field_g<DT, NCH>(st, Cw, h2, t + 2, d, Cp, C, lane, Fl);
   } else {
     zero<NCH>(Fl);  // past the last row
@@ -452,43 +458,49 @@ __device__ __forceinline__ void rows_replica_g(const StructArgs &a, int r, uint3
     int t = 1;
     int hn = hot[1];
     const RowTest rtst{B, twoA, len, C};
-    while (true) {
-      // Rows the whole-row test clears change nothing, so four of them run
-      // with the fields' roles rotated, (P, N, F_{t+2}) = (X0, X2, X3), (X1,
-      // X3, X0), (X2, X0, X1), (X3, X1, X2), and move no register; a row that
-      // may flip leaves the cycle with `from` = its place in it, and its
-      // fields are rotated into P = X0, Cu = X1, N = X2, F_{t+2} = X3.
-      int rt, xn[NCH], from;
-      if (rows_g_front<DT, NCH, K>(st, hot, ring, d, Cp, C, Cw, lane, t, hn, X0, X2, X3, tAc, rtst, rt, xn)) {
-        from = 0;
-      } else {
-        if (++t >= C) break;
+    int rt, xn[NCH];
+    if (len <= A) {
+      // A cold sweep: a row whose cells form a permutation with the rest of
+      // the state has every dE >= A >= len, so almost every row is cleared
+      // by the whole-row test and changes nothing.  Four of them run with
+      // the fields' roles rotated, (P, N, F_{t+2}) = (X0, X2, X3), (X1, X3,
+      // X0), (X2, X0, X1), (X3, X1, X2), so no register moves; this loop
+      // holds no flip path (which keeps its registers free), and the first
+      // row that may flip rotates its fields into P = X0, Cu = X1, N = X2,
+      // F_{t+2} = X3 and finishes the sweep in the loop below.
+      while (true) {
+        if (rows_g_front<DT, NCH, K>(st, hot, ring, d, Cp, C, Cw, lane, t, hn, X0, X2, X3, tAc, rtst, rt, xn))
+          goto flip;
+        if (++t >= C) goto sweep_done;
         hn = hot[t];
         if (rows_g_front<DT, NCH, K>(st, hot, ring, d, Cp, C, Cw, lane, t, hn, X1, X3, X0, tAc, rtst, rt, xn)) {
-          from = 1;
-        } else {
-          if (++t >= C) break;
-          hn = hot[t];
-          if (rows_g_front<DT, NCH, K>(st, hot, ring, d, Cp, C, Cw, lane, t, hn, X2, X0, X1, tAc, rtst, rt, xn)) {
-            from = 2;
-          } else {
-            if (++t >= C) break;
-            hn = hot[t];
-            if (rows_g_front<DT, NCH, K>(st, hot, ring, d, Cp, C, Cw, lane, t, hn, X3, X1, X2, tAc, rtst, rt, xn)) {
-              from = 3;
-            } else {
-              if (++t >= C) break;
-              hn = hot[t];
-              continue;
-            }
-          }
+          rotate_fields<NCH>(X0, X1, X2, X3);
+          goto flip;
         }
+        if (++t >= C) goto sweep_done;
+        hn = hot[t];
+        if (rows_g_front<DT, NCH, K>(st, hot, ring, d, Cp, C, Cw, lane, t, hn, X2, X0, X1, tAc, rtst, rt, xn)) {
+          swap_fields<NCH>(X0, X2);
+          swap_fields<NCH>(X1, X3);
+          goto flip;
+        }
+        if (++t >= C) goto sweep_done;
+        hn = hot[t];
+        if (rows_g_front<DT, NCH, K>(st, hot, ring, d, Cp, C, Cw, lane, t, hn, X3, X1, X2, tAc, rtst, rt, xn)) {
+          rotate_fields<NCH>(X3, X2, X1, X0);
+          goto flip;
+        }
+        if (++t >= C) goto sweep_done;
+        hn = hot[t];
       }
-      if (from == 1) rotate_fields<NCH>(X0, X1, X2, X3);
-      else if (from == 2) { swap_fields<NCH>(X0, X2); swap_fields<NCH>(X1, X3); }
-      else if (from == 3) rotate_fields<NCH>(X3, X2, X1, X0);
-      any_hit |= rows_g_flip<DT, NCH>(a, st, hot, d, Cp, C, Cw, lane, t, s, hn, rt, xn, X0, X1, X2, tAc, validc, E,
-                                      acc, viol, twoA, len, lenm1, cT, dq, Q, thr, rg);
+    }
+    // a hot sweep (most rows may flip): P = X0, Cu = X1, N = X2, F_{t+2} = X3
+    while (true) {
+      if (rows_g_front<DT, NCH, K>(st, hot, ring, d, Cp, C, Cw, lane, t, hn, X0, X2, X3, tAc, rtst, rt, xn)) {
+      flip:
+        any_hit |= rows_g_flip<DT, NCH>(a, st, hot, d, Cp, C, Cw, lane, t, s, hn, rt, xn, X0, X1, X2, tAc, validc,
+                                        E, acc, viol, twoA, len, lenm1, cT, dq, Q, thr, rg);
+      }
 #pragma unroll
       for (int c = 0; c < NCH; ++c)
 #pragma unroll
@@ -500,6 +512,7 @@ __device__ __forceinline__ void rows_replica_g(const StructArgs &a, int r, uint3
       if (++t >= C) break;
       hn = hot[t];
     }
+  sweep_done:
     cp_async_wait<0>();  // the next sweep refills every slot
     __syncwarp();
     if (viol == 0 && E < best) best = E;
