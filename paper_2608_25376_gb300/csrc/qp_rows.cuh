@@ -154,6 +154,36 @@ __device__ __forceinline__ bool row_pretest(const int (&P)[NCH][4], const int (&
   return maybe;
 }
 
+// row_pretest with the column term kept shifted, tAc = 2A c_i - len: base -
+// lo = B f + tAc + 2A(r-1), one add fewer per column when r = 1 (the common
+// case: a row that holds exactly one cell).  Same result as row_pretest.
+// W1 = hi - lo for r = 1, i.e. 4A - 2 len (fixed through a sweep; used when
+// len <= 2A, else every column passes).
+template <int NCH>
+__device__ __forceinline__ bool row_pretest_shifted(const int (&P)[NCH][4], const int (&N)[NCH][4],
+                                                    const int (&tAc)[NCH][4], int B, int twoA, int rt, int len,
+                                                    unsigned W1) {
+  bool maybe = false;
+  if (B == 1 && rt == 1) {
+    if (len > twoA) return true;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) maybe |= (unsigned)P[c][j] + (unsigned)N[c][j] + (unsigned)tAc[c][j] > W1;
+  } else {
+    const int lo = len - twoA * (rt - 1), hi = twoA * (3 - rt) - len;
+    if (hi < lo) return true;
+    const unsigned W = (unsigned)(hi - lo);
+    const unsigned adj = (unsigned)(twoA * (rt - 1));
+#pragma unroll
+    for (int c = 0; c < NCH; ++c)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        maybe |= (unsigned)B * ((unsigned)P[c][j] + (unsigned)N[c][j]) + (unsigned)tAc[c][j] + adj > W;
+  }
+  return maybe;
+}
+
 // The proposals of one 128-wide row chunk when at least one of them can be
 // accepted or needs a draw: evaluate against the current row sum, take the
 // first accepted one, apply it, resume after it.  Returns whether any flip was
@@ -165,7 +195,7 @@ __device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int
                                        int (&tAc)[4], int &rt, int (&Cu)[NCH][4], uint32_t *row, long long &E,
                                        long long &acc, int &viol, const void *d, int Cp, int C, int lane, int twoA,
                                        int len, unsigned lenm1, float cT, int dq, uint32_t Q, const uint32_t *thr,
-                                       uint32_t rg, uint32_t key0, uint32_t key1) {
+                                       uint32_t rg, uint32_t key0, uint32_t key1, int tshift = 0) {
   const int ib = 128 * c + 4 * lane;
   const int delta = tC & 3;
   int cand = validc;
@@ -228,7 +258,7 @@ __device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int
     const int L = __ffs(bal) - 1;
     const int jl = accm ? __ffs(accm) - 1 : 0;
     const int xl = (xnc >> jl) & 1;
-    const int tc = sel4(tAc, jl);
+    const int tc = sel4(tAc, jl) + tshift;  // 2A c_i
     const int pk0 = jl | (xl << 2) | ((tc == twoA) << 3) | ((tc + (1 - 2 * xl) * twoA == twoA) << 4);
     const int de = __shfl_sync(kFull, sel4(dE, jl), L);
     const int pk = __shfl_sync(kFull, pk0, L);

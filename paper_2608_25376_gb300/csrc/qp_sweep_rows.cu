@@ -274,6 +274,7 @@ __device__ __forceinline__ void ring_issue(const int16_t *hot, DT *ring, const v
 // The parameters of the whole-row test that stay fixed through a sweep.
 struct RowTest {
   int B, twoA, len, C;
+  unsigned W1;  // 4A - 2 len: the range width of the test when r = 1
 };
 
 // X0 <- X1 <- X2 <- X3 <- X0
@@ -342,7 +343,7 @@ __device__ __forceinline__ bool rows_g_front(const uint32_t *st, const int16_t *
     }
     rt = __reduce_add_sync(kFull, rt);
   }
-  return __any_sync(kFull, row_pretest<NCH>(P, N, tAc, rtst.B, rtst.twoA, rt, rtst.len, rtst.C));
+  return __any_sync(kFull, row_pretest_shifted<NCH>(P, N, tAc, rtst.B, rtst.twoA, rt, rtst.len, rtst.W1));
 }
 
 // The back half of a row that may flip (P = F_{t-1}, Cu = F_t, N = F_{t+1}):
@@ -377,7 +378,7 @@ __device__ __forceinline__ bool rows_g_flip(const StructArgs &a, uint32_t *st, i
       const int k0 = twoA * (rt - 1), k1 = twoA * (3 - rt);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        base[j] = B * (P[c][j] + N[c][j]) + tAc[c][j];
+        base[j] = B * (P[c][j] + N[c][j]) + tAc[c][j] + len;
         de[j] = ((xn[c] >> j) & 1) ? k1 - base[j] : base[j] + k0;
         hit |= (unsigned)(de[j] < len) << j;
       }
@@ -386,7 +387,7 @@ __device__ __forceinline__ bool rows_g_flip(const StructArgs &a, uint32_t *st, i
       any_hit = true;
       flipped |= row_chunk<DT, NCH, 0, true>(c, t, s, tC, base, de, xn[c], validc[c], tAc[c], rt, Cu, row, E, acc,
                                              viol, d, Cp, C, lane, twoA, len, lenm1, cT, dq, Q, thr, rg, a.key0,
-                                             a.key1);
+                                             a.key1, len);
     }
   }
   viol += (rt != 1) - (rt0 != 1);
@@ -428,6 +429,7 @@ __device__ __forceinline__ void rows_replica_g(const StructArgs &a, int r, uint3
   long long E;
   int viol;
   rows_init<DT, NCH, 0, true>(a, r, st, hot, d, lane, tAc, validc, E, viol, !fresh);
+  int tl = 0;  // tAc holds 2A c_i - tl (shifted by the sweep's table length)
 
   const int lev = a.level ? __ldg(a.level + r) : -1;
   bool settled = false;
@@ -442,6 +444,13 @@ __device__ __forceinline__ void rows_replica_g(const StructArgs &a, int r, uint3
     const float cT = a.thr_c[ts];
     const int dq = len > 1 ? min(len - 1, max(1, (int)fminf(8.0f / cT, 1.0e9f))) : 1;
     const uint32_t Q = len > 1 ? __ldg(a.thr + a.thr_off[ts] + dq) : 0u;
+    if (len != tl) {  // tAc holds 2A c_i - len for this sweep's len
+#pragma unroll
+      for (int c = 0; c < NCH; ++c)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tAc[c][j] += tl - len;
+      tl = len;
+    }
     // X0..X3 hold the fields of rows t-1, t, t+1 and t+2 (the last read from
     // the ring) in roles that rotate by one per row
     int X0[NCH][4], X1[NCH][4], X2[NCH][4], X3[NCH][4];
@@ -457,7 +466,7 @@ __device__ __forceinline__ void rows_replica_g(const StructArgs &a, int r, uint3
     }
     int t = 1;
     int hn = hot[1];
-    const RowTest rtst{B, twoA, len, C};
+    const RowTest rtst{B, twoA, len, C, (unsigned)(2 * twoA - 2 * len)};
     int rt, xn[NCH];
     if (len <= A) {
       // A cold sweep: a row whose cells form a permutation with the rest of
