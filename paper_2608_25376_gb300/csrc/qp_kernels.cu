@@ -482,7 +482,38 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_sweep_dense(const Dens
     const int len = a.thr_len[s];
     const float cT = a.thr_c[s];
     int pos = 0;
+    const int lenq = len > 1 ? len : 1;  // a proposal matters if dE < len, or dE <= 0
     for (int m0 = 0; m0 < nblk; m0 += 32) {
+      // Four groups of 128 proposals at once, when they start a block of four:
+      // independent loads of their local fields and one vote; if no proposal
+      // there has dE < len (none can be accepted, none needs a draw) the four
+      // groups change nothing and are passed over.  Earlier flips are all
+      // before them (pos <= their first proposal).
+      if ((m0 & 127) == 0) {
+        bool matters = false;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const int mg = m0 + 32 * g + lane;
+          if (mg < nblk) {
+            const int kg = mg << 2;
+            const uint32_t xg = (st[kg >> 5] >> (kg & 31)) & 0xFu;
+            const uint32_t fg = (fz[kg >> 5] >> (kg & 31)) & 0xFu;
+            const int ing = n - kg >= 4 ? 0xF : ((1 << (n - kg)) - 1);
+            const int vg = (int)(~fg & 0xFu) & ing;
+            const int4 hg = *reinterpret_cast<const int4 *>(h + kg);
+            const int hh[4] = {hg.x, hg.y, hg.z, hg.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int dEj = ((xg >> j) & 1) ? -hh[j] : hh[j];
+              matters |= ((vg >> j) & 1) && dEj < lenq;
+            }
+          }
+        }
+        if (!__any_sync(kFull, matters)) {
+          m0 += 96;
+          continue;
+        }
+      }
       const int m = m0 + lane;
       const int k0 = m << 2;
       uint32_t xn = 0;
