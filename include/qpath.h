@@ -499,6 +499,16 @@ qp_status qp_ws_expected_steps(const float *logits, int32_t ld, int32_t M, const
                                void *cuda_stream);
 qp_status qp_ws_walk(qp_handle *h, const float *score, int32_t slack, uint8_t *state_out, int32_t *path_out,
                      int64_t *length_out, void *cuda_stream);
+/* qp_ws_greedy: qp_ws_decode on the device.  logits (C rows of stride ld >= C,
+ * fp32, finite), state_out (C*C bytes, zeroed then one 1 per step) and
+ * path_out (C int32) are device buffers (either output may be NULL, not
+ * both); 1 <= C <= 256, 0 <= start_cell < C (QP_EINVAL otherwise, and for
+ * host buffers or buffers smaller than the call needs).  Step 0 is the start
+ * cell; then the largest logit over the unassigned cells and the free steps
+ * 1..C-1 fixes one (cell, step) pair at a time, ties to the smaller cell,
+ * then the smaller step.  One CTA; asynchronous on the stream. */
+qp_status qp_ws_greedy(const float *logits, int32_t ld, int32_t C, int32_t start_cell, uint8_t *state_out,
+                       int32_t *path_out, void *cuda_stream);
 
 /* Self-test of the bounded wait that guards the library's asynchronous copies
  * (no counterpart in the paper): one warp waits on an mbarrier phase that

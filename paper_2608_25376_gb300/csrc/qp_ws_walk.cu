@@ -1,7 +1,8 @@
 // Device decode of the learned warm start: the expected step of every cell
-// under its step logits, and the walk that turns a field (with or without a
-// per-cell score) into a feasible one-hot seed.  The public contract is in
-// include/qpath.h (qp_ws_expected_steps, qp_ws_walk).
+// under its step logits, the walk that turns a field (with or without a
+// per-cell score) into a feasible one-hot seed, and the greedy matching of
+// cells to steps.  The public contract is in include/qpath.h
+// (qp_ws_expected_steps, qp_ws_walk, qp_ws_greedy).
 //
 // Walk: from the start cell, step t goes to a cell not yet on the path.  The
 // candidates are the unvisited cells within `slack` of the nearest unvisited
@@ -121,6 +122,78 @@ __global__ void __launch_bounds__(32) k_ws_walk(const int32_t *d, int C, int sta
   if (lane == 0 && length) *length = L;
 }
 
+// Greedy matching of cells to steps (the device form of qp_ws_decode): step 0
+// is the start cell; each round fixes the (cell, step) pair with the largest
+// logit over the unassigned cells and the free steps 1..C-1, ties to the
+// smaller cell, then the smaller step.  One CTA, one thread per cell: a
+// thread keeps its cell's best free step (the smaller step on equal logits);
+// a round is a block-wide maximum of (logit, -cell), after which the cells
+// whose best step was just taken scan their row again.
+constexpr int kGreedyThreads = 256;
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(kFull, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(kGreedyThreads) k_ws_greedy(const float *Z, int ld, int C, int start,
+                                                              uint8_t *state, int32_t *path) {
+  __shared__ unsigned char step_done[kGreedyThreads];
+  __shared__ int32_t pth[kGreedyThreads];
+  __shared__ unsigned long long wmax[kGreedyThreads / 32];
+  __shared__ int32_t taken;
+  const int i = threadIdx.x, lane = i & 31, warp = i >> 5;
+  step_done[i] = (i == 0 || i >= C) ? 1 : 0;
+  if (i == 0) pth[0] = start;
+  bool open = i < C && i != start;
+  __syncthreads();
+  const float *zi = Z + (size_t)min(i, C - 1) * ld;
+  int bt = -1;
+  float bv = 0.0f;
+  auto rescan = [&]() {
+    bt = -1;
+    for (int t = 1; t < C; ++t) {
+      if (step_done[t]) continue;
+      const float v = __ldg(zi + t);
+      if (bt < 0 || v > bv) {
+        bt = t;
+        bv = v;
+      }
+    }
+  };
+  if (open) rescan();
+  for (int round = 1; round < C; ++round) {
+    // keys are > 0 for finite logits; the low bits prefer the smaller cell
+    const unsigned long long key =
+        open ? ((unsigned long long)float_key(bv) << 32) | (unsigned)(0xFFFFu - (unsigned)i) : 0ull;
+    const unsigned long long wm = warp_max_u64(key);
+    if (lane == 0) wmax[warp] = wm;
+    __syncthreads();
+    unsigned long long m = wmax[0];
+#pragma unroll
+    for (int w = 1; w < kGreedyThreads / 32; ++w) m = wmax[w] > m ? wmax[w] : m;
+    const int bi = (int)(0xFFFFu - (unsigned)(m & 0xFFFFu));
+    if (i == bi) {
+      taken = bt;
+      pth[bt] = i;
+      step_done[bt] = 1;
+      open = false;
+    }
+    __syncthreads();
+    if (open && bt == taken) rescan();
+  }
+  __syncthreads();
+  if (i < C) {
+    const int c = pth[i];
+    if (path) path[i] = c;
+    if (state) state[(size_t)i * C + c] = 1;
+  }
+}
+
 }  // namespace
 }  // namespace qp
 
@@ -169,6 +242,30 @@ extern "C" qp_status qp_ws_walk(qp_handle *h, const float *score, int32_t slack,
     e = cudaGetLastError();
   }
   if (prev != v.dev) cudaSetDevice(prev);
+  if (e != cudaSuccess) return set_error(QP_ECUDA, cudaGetErrorString(e));
+  return QP_OK;
+}
+
+extern "C" qp_status qp_ws_greedy(const float *logits, int32_t ld, int32_t C, int32_t start_cell, uint8_t *state_out,
+                                  int32_t *path_out, void *stream) {
+  using namespace qp;
+  clear_error();
+  if (!logits || C < 1 || C > kGreedyThreads || start_cell < 0 || start_cell >= C || ld < C ||
+      (!state_out && !path_out))
+    return set_error(QP_EINVAL, "qp_ws_greedy: bad argument");
+  if (!device_pointer(logits) || (state_out && !device_pointer(state_out)) || (path_out && !device_pointer(path_out)))
+    return set_error(QP_EINVAL, "qp_ws_greedy: every buffer must be device memory");
+  if (!device_range_fits(logits, ((size_t)(C - 1) * ld + C) * 4) ||
+      (state_out && !device_range_fits(state_out, (size_t)C * C)) ||
+      (path_out && !device_range_fits(path_out, (size_t)C * 4)))
+    return set_error(QP_EINVAL, "qp_ws_greedy: a device buffer is smaller than the call needs");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (state_out) e = cudaMemsetAsync(state_out, 0, (size_t)C * C, st);
+  if (e == cudaSuccess) {
+    k_ws_greedy<<<1, kGreedyThreads, 0, st>>>(logits, ld, C, start_cell, state_out, path_out);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return set_error(QP_ECUDA, cudaGetErrorString(e));
   return QP_OK;
 }

@@ -32,7 +32,7 @@ SYMBOLS = ["qp_build_qubo", "qp_build_from_dense", "qp_qubo_info", "qp_export_de
            "qp_batch_run", "qp_batch_info", "qp_batch_destroy", "qp_anneal_batch", "qp_decode_path",
            "qp_decode_batch", "qp_repair_batch", "qp_repair_path", "qp_anneal_timed", "qp_anneal_pt", "qp_ws_create", "qp_ws_destroy", "qp_ws_param_count", "qp_ws_get_params",
            "qp_ws_set_params", "qp_ws_features", "qp_ws_forward", "qp_ws_set_forward_mode", "qp_ws_grads", "qp_ws_train_step",
-           "qp_ws_get_state", "qp_ws_get_buffer", "qp_ws_expected_steps", "qp_ws_walk",
+           "qp_ws_get_state", "qp_ws_get_buffer", "qp_ws_expected_steps", "qp_ws_walk", "qp_ws_greedy",
            "qp_ws_decode", "qp_ws_decode_walk", "qp_ws_infer", "qp_selftest_wait", "qp_device_checks", "qp_destroy",
            "qp_last_error"]
 
@@ -118,6 +118,7 @@ def lib():
                 "qp_ws_get_state": [vp, i32, vp],
                 "qp_ws_expected_steps": [vp, i32, i32, vp, vp, vp],
                 "qp_ws_walk": [vp, vp, i32, vp, vp, vp, vp],
+                "qp_ws_greedy": [vp, i32, i32, i32, vp, vp, vp],
                 "qp_ws_get_buffer": [vp, i32, i32, vp],
                 "qp_ws_decode": [vp, i32, i32, i32, vp, vp],
                 "qp_ws_decode_walk": [vp, i32, i32, i32, vp, vp, vp],
@@ -583,6 +584,18 @@ def qp_ws_walk(h: Handle, score=None, slack=0, state_out=None, path_out=None, le
     ln = torch.empty(1, dtype=torch.int64, device=dev) if length_out is None else length_out
     _check(lib().qp_ws_walk(h.ptr, _ptr(score), int(slack), _ptr(st), _ptr(pa), _ptr(ln), _stream(stream)))
     return st, pa, ln
+
+
+def qp_ws_greedy(logits, C, start_cell, state_out=None, path_out=None, stream=None):
+    """The greedy matching decode (qp_ws_decode) on the device: logits a device
+    float32 tensor [C', ld] with C' >= C rows; -> (state uint8 [C*C], path int32
+    [C]), device tensors (allocated when not given)."""
+    import torch
+    ld = logits.shape[1]
+    st = torch.empty(C * C, dtype=torch.uint8, device=logits.device) if state_out is None else state_out
+    pa = torch.empty(C, dtype=torch.int32, device=logits.device) if path_out is None else path_out
+    _check(lib().qp_ws_greedy(_ptr(logits), int(ld), int(C), int(start_cell), _ptr(st), _ptr(pa), _stream(stream)))
+    return st, pa
 
 
 def qp_selftest_wait() -> dict:

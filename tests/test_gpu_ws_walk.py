@@ -82,3 +82,39 @@ def test_walk_refuses_host_buffers(dev):
     with pytest.raises(qpath.QpError) as e:
         qpath.qp_ws_walk(h, None, 0, np.zeros(81, np.uint8), np.zeros(9, np.int32), np.zeros(1, np.int64))
     assert e.value.status == qpath.QP_EINVAL
+
+
+@pytest.mark.parametrize("C,ld,seed", [(1, 1, 0), (2, 2, 1), (7, 256, 2), (64, 64, 3), (131, 256, 4), (256, 256, 5),
+                                       (200, 203, 6)])
+def test_greedy_decode_on_device_matches_reference(dev, C, ld, seed):
+    """qp_ws_greedy against the host decode and, up to 64 cells, the plain CPU
+    restatement, path for path, on logits with ties (equal values in one row,
+    across rows, and -0 against +0)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    logits = np.round(rng.normal(0, 2, size=(C, ld)), 1).astype(np.float32)  # coarse values: many ties
+    if C > 4:
+        logits[1, 2] = -0.0
+        logits[3, 2] = 0.0
+        logits[2, 1:4] = logits.max() + 1  # one row's maximum at three steps
+    start = int(rng.integers(C))
+    st, path = qpath.qp_ws_greedy(torch.from_numpy(logits).cuda(), C, start)
+    torch.cuda.synchronize()
+    path = path.cpu().numpy().tolist()
+    _, host = qpath.qp_ws_decode(logits, C, start)
+    assert path == host.tolist()
+    if C <= 64:
+        assert path == mlp_ref.greedy_decode(logits, C, start)
+    x = st.cpu().numpy().reshape(C, C)
+    assert (x.sum(axis=0) == 1).all() and (x.sum(axis=1) == 1).all() and x[0, start] == 1
+
+
+def test_greedy_decode_refuses_bad_arguments(dev):
+    import torch
+    Z = torch.zeros((8, 8), dtype=torch.float32, device="cuda")
+    with pytest.raises(qpath.QpError):
+        qpath.qp_ws_greedy(Z, 9, 0)  # a row stride shorter than the field
+    with pytest.raises(qpath.QpError):
+        qpath.qp_ws_greedy(Z.cpu(), 8, 0)  # host logits
+    with pytest.raises(qpath.QpError):
+        qpath.qp_ws_greedy(Z, 8, 8)  # start outside the field

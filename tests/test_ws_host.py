@@ -212,3 +212,17 @@ def test_expected_steps_reference_closed_forms():
     Z[2, 17] = 800.0
     E = mlp_ref.expected_steps(Z, [1, 40, 90])
     assert E[0] == 0.0 and abs(E[1] - 19.5) < 1e-12 and abs(E[2] - 17.0) < 1e-12
+
+
+@pytest.mark.parametrize("logits,start,path", [
+    # the two largest free entries tie (5 at step 1 for cells 0 and 2): the smaller cell takes step 1
+    ([[0, 5, 1], [9, 9, 9], [0, 5, 2]], 1, [1, 0, 2]),
+    # the largest entry (7) fixes cell 0 at step 2 first; cell 2 then takes step 1 although 6 < 7
+    ([[0, 1, 7], [9, 9, 9], [0, 6, 3]], 1, [1, 2, 0]),
+    # within one cell, equal logits go to the smaller step; the start's row and step 0 never count
+    ([[9, 9, 9, 9], [0, 4, 4, 4], [0, 1, 2, 3], [99, 0, 0, 1]], 0, [0, 1, 3, 2]),
+])
+def test_greedy_decode_hand_worked(logits, start, path):
+    """Pins of the plain greedy matching, worked by hand from its definition."""
+    L = np.asarray(logits, np.float32)
+    assert mlp_ref.greedy_decode(L, L.shape[0], start) == path
