@@ -149,6 +149,25 @@ qp_status qp_build_qubo(const qp_field *field, int32_t A, int32_t B, int32_t sca
  * frozen_val (NULL = 0).  The dense form of Eq. 6 is one such QUBO.
  * Errors: QP_EINVAL (n < 1, S not symmetric), QP_ERANGE (a row's absolute sum
  * beyond int32), QP_ENOMEM, QP_ECUDA. */
+/* The extended objective (Section V names battery capacity and the pesticide
+ * amount as the next objectives and gives no formula; the reading here): the
+ * distance term of Eq. 3 with one weight per leg,
+ *   E(x) = sum_{t<C-1} w_t sum_{i,j} d_ij x_{t,i} x_{t+1,j} + the penalties,
+ * where w_t stands for the mass carried on the leg from step t to t+1 (a fixed
+ * amount sprayed per cell, flight energy taken proportional to mass times
+ * distance).  leg_weights: n_legs = C - 1 non-negative int32, host memory,
+ * copied.  A <= 0 selects A = 2 * max w * max d.  The handle holds the dense
+ * form (QP_DENSE) and the distance matrix; it anneals with QP_KERNEL_DENSE
+ * (QP_KERNEL_AUTO picks it), decodes like any field handle (qp_decode_path,
+ * qp_decode_batch: the length reported is the unweighted one) and works with
+ * qp_ws_walk.  The structured-form calls refuse it (QP_EINVAL): the structured
+ * kernels of qp_anneal_ex, qp_anneal_noalloc, qp_anneal_pt, qp_anneal_timed,
+ * the batch and the repair (whose 2-opt shortens the unweighted length).
+ * Errors as qp_build_qubo; QP_EINVAL also for NULL or device weights, a wrong
+ * count or a negative weight. */
+qp_status qp_build_qubo_weighted(const qp_field *field, int32_t A, const int32_t *leg_weights, int32_t n_legs,
+                                 int32_t scale, qp_handle **out);
+
 qp_status qp_build_from_dense(const int32_t *S, int64_t n, const uint8_t *frozen,
                               const uint8_t *frozen_val, int64_t c0, qp_handle **out);
 

@@ -58,6 +58,10 @@ def lib():
             L.or_energy_terms.argtypes = [i32, P(i32), i32, i32, P(ct.c_uint8), P(i64), P(i64), P(i64)]
             L.or_dense_qubo.restype = None
             L.or_dense_qubo.argtypes = [i32, P(i32), i32, i32, P(i32), P(i64)]
+            L.or_energy_terms_weighted.restype = i64
+            L.or_energy_terms_weighted.argtypes = [i32, P(i32), i32, P(i32), P(ct.c_uint8)]
+            L.or_dense_qubo_weighted.restype = None
+            L.or_dense_qubo_weighted.argtypes = [i32, P(i32), i32, P(i32), P(i32), P(i64)]
             L.or_energy_dense.restype = i64
             L.or_energy_dense.argtypes = [i64, P(i32), i64, P(ct.c_uint8)]
             L.or_philox4x32_10.restype = None
@@ -159,6 +163,31 @@ def dense_qubo(d, A, B):
     S = np.zeros((n, n), np.int32)
     c0 = np.zeros(1, np.int64)
     lib().or_dense_qubo(C, _p(d, ct.c_int32), int(A), int(B), _p(S, ct.c_int32), _p(c0, ct.c_int64))
+    return S, int(c0[0])
+
+
+def energy_terms_weighted(d, A, w, x):
+    """Reading R9: Eq. 6 with leg weights w[0..C-2] on the distance term."""
+    d = np.ascontiguousarray(d, np.int32)
+    C = d.shape[0]
+    w = np.ascontiguousarray(w, np.int32)
+    assert w.size == C - 1
+    x = np.ascontiguousarray(x, np.uint8).reshape(-1)
+    assert x.size == C * C
+    return int(lib().or_energy_terms_weighted(C, _p(d, ct.c_int32), int(A), _p(w, ct.c_int32), _p(x, ct.c_uint8)))
+
+
+def dense_qubo_weighted(d, A, w):
+    """Reading R9: the dense form of energy_terms_weighted -> (S, c0)."""
+    d = np.ascontiguousarray(d, np.int32)
+    C = d.shape[0]
+    w = np.ascontiguousarray(w, np.int32)
+    assert w.size == C - 1
+    n = C * C
+    S = np.zeros((n, n), np.int32)
+    c0 = np.zeros(1, np.int64)
+    lib().or_dense_qubo_weighted(C, _p(d, ct.c_int32), int(A), _p(w, ct.c_int32), _p(S, ct.c_int32),
+                                 _p(c0, ct.c_int64))
     return S, int(c0[0])
 
 

@@ -30,6 +30,13 @@
  *     the state is feasible (every row and column sum is 1); INT64_MAX if none.
  *     A QUBO without path structure has no feasibility test: every sweep end
  *     counts.
+ *  R9 extended objective (Section V names battery capacity and the pesticide
+ *     amount as the next objectives and gives no formula): the distance term
+ *     of Eq. 3 with one integer weight per leg, sum_t w_t d_ij x_{t,i}
+ *     x_{t+1,j} (w_t = B for every t is Eq. 3 itself).  With a fixed amount
+ *     sprayed per cell the mass carried on leg t falls with t, and a leg's
+ *     flight energy is taken as proportional to mass times distance; the
+ *     weights are that mass in integer units.
  */
 #include <math.h>
 #include <pthread.h>
@@ -145,6 +152,56 @@ void or_dense_qubo(int32_t C, const int32_t *d, int32_t A, int32_t B,
           if (u == t) v += 2 * A;            /* same step: Eq. 5 */
           if (j == i) v += 2 * A;            /* same cell: Eq. 4 */
           if (u == t + 1 || u == t - 1) v += B * d[(int64_t)i * C + j]; /* Eq. 3 */
+          S[k * n + l] = v;
+        }
+      }
+    }
+  }
+  *c0 = 2 * (int64_t)A * C;
+}
+
+/* R9: Eq. 6 with the distance term weighted per leg, w[t] on the leg from
+ * step t to step t+1 (t = 0..C-2); the penalty terms as in Eqs. 4-5.        */
+int64_t or_energy_terms_weighted(int32_t C, const int32_t *d, int32_t A, const int32_t *w,
+                                 const uint8_t *x) {
+  int64_t hd = 0, hv = 0, ht = 0;
+  for (int32_t t = 0; t + 1 < C; ++t)
+    for (int32_t i = 0; i < C; ++i)
+      for (int32_t j = 0; j < C; ++j)
+        hd += (int64_t)w[t] * d[(int64_t)i * C + j] * x[(int64_t)t * C + i] *
+              x[(int64_t)(t + 1) * C + j];
+  for (int32_t i = 0; i < C; ++i) {
+    int64_t s = 0;
+    for (int32_t t = 0; t < C; ++t) s += x[(int64_t)t * C + i];
+    hv += (1 - s) * (1 - s);
+  }
+  for (int32_t t = 0; t < C; ++t) {
+    int64_t s = 0;
+    for (int32_t i = 0; i < C; ++i) s += x[(int64_t)t * C + i];
+    ht += (1 - s) * (1 - s);
+  }
+  return hd + (int64_t)A * (hv + ht);
+}
+
+/* R9: the dense form of or_energy_terms_weighted, expanded as or_dense_qubo
+ * expands Eq. 6: the pair of consecutive steps t, t+1 gets w[t] d_ij.        */
+void or_dense_qubo_weighted(int32_t C, const int32_t *d, int32_t A, const int32_t *w,
+                            int32_t *S, int64_t *c0) {
+  int64_t n = (int64_t)C * C;
+  memset(S, 0, sizeof(int32_t) * n * n);
+  for (int32_t t = 0; t < C; ++t) {
+    for (int32_t i = 0; i < C; ++i) {
+      int64_t k = (int64_t)t * C + i;
+      S[k * n + k] = -2 * A;
+      for (int32_t u = 0; u < C; ++u) {
+        for (int32_t j = 0; j < C; ++j) {
+          int64_t l = (int64_t)u * C + j;
+          if (l == k) continue;
+          int32_t v = 0;
+          if (u == t) v += 2 * A;
+          if (j == i) v += 2 * A;
+          if (u == t + 1) v += w[t] * d[(int64_t)i * C + j];
+          if (u == t - 1) v += w[u] * d[(int64_t)i * C + j];
           S[k * n + l] = v;
         }
       }

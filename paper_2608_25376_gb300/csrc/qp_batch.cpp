@@ -52,6 +52,7 @@ extern "C" qp_status qp_batch_create(qp_handle *const *hs, int32_t count, int32_
   for (int f = 0; f < count; ++f) {
     const qp_handle *h = hs[f];
     if (!h || !h->path) return fail(QP_EINVAL, "field %d: a batch needs handles built by qp_build_qubo", f);
+    if (h->weighted) return fail(QP_EINVAL, "field %d: the batch sweep is unweighted (a handle with leg weights)", f);
     if (h->dev != b->dev) return fail(QP_EINVAL, "field %d lives on another device", f);
     if (!h->d_i16) return fail(QP_ERANGE, "field %d: a batch needs int16 distances", f);
     if (!is_device_ptr(states_out[f]) || !is_device_ptr(energies_out[f]) ||

@@ -272,14 +272,17 @@ qp_status upload_bits(qp_handle *h, const std::vector<uint8_t> &fr, const std::v
 }  // namespace
 
 // --------------------------------------------------------------------------- build
-extern "C" qp_status qp_build_qubo(const qp_field *f, int32_t A, int32_t B, int32_t scale,
-                                   int32_t flags, qp_handle **out) {
+// The path QUBO of a field; w (host, n_legs entries) replaces B on the
+// distance term leg by leg when given (the dense form only).
+static qp_status build_field_qubo(const qp_field *f, int32_t A, int32_t B, int32_t scale, int32_t flags,
+                                  const int32_t *w, int32_t n_legs, qp_handle **out) {
   g_err.clear();
   if (!f || !out) return fail(QP_EINVAL, "field and out must not be NULL");
   *out = nullptr;
   if (f->rows < 1 || f->cols < 1 || (int64_t)f->rows * f->cols > (1 << 24))
     return fail(QP_EINVAL, "bad grid size %d x %d", f->rows, f->cols);
   if (B < 0 || scale < 1) return fail(QP_EINVAL, "need B >= 0 and scale >= 1");
+  if (w && is_device_ptr(w)) return fail(QP_EINVAL, "leg weights must be host memory");
   if (f->start < 0 || f->start >= f->rows * f->cols) return fail(QP_EINVAL, "start out of the grid");
   if (f->free_mask && !f->free_mask[f->start]) return fail(QP_EINVAL, "start cell is an obstacle");
   if (flags == 0) flags = QP_STRUCTURED;
@@ -300,6 +303,17 @@ extern "C" qp_status qp_build_qubo(const qp_field *f, int32_t A, int32_t B, int3
   const int C = (int)cr.size();
   if (C < 2) return fail(QP_EINVAL, "a field needs at least 2 free cells (has %d)", C);
   if (C > kMaxCells) return fail(QP_ERANGE, "%d cells exceed the limit %d", C, kMaxCells);
+  int64_t maxw = B;  // the largest weight on any leg
+  if (w) {
+    if (n_legs != C - 1) return fail(QP_EINVAL, "need C - 1 = %d leg weights (got %d)", C - 1, n_legs);
+    maxw = 0;
+    for (int t = 0; t < C - 1; ++t) {
+      if (w[t] < 0) return fail(QP_EINVAL, "leg weight %d is negative", t);
+      maxw = std::max<int64_t>(maxw, w[t]);
+    }
+    flags |= QP_DENSE;
+    h->weighted = true;
+  }
   h->path = true;
   h->C = C;
   h->n = (int64_t)C * C;
@@ -314,13 +328,13 @@ extern "C" qp_status qp_build_qubo(const qp_field *f, int32_t A, int32_t B, int3
       maxd = std::max(maxd, v);
     }
   h->max_d = (int32_t)maxd;
-  const int64_t Aeff = A > 0 ? A : 2 * maxd;
+  const int64_t Aeff = A > 0 ? A : 2 * maxd * (w ? std::max<int64_t>(1, maxw) : 1);
   if (Aeff > INT32_MAX / 4) return fail(QP_ERANGE, "penalty A beyond int32/4");
   h->A = (int32_t)Aeff;
   h->B = B;
   h->c0 = 2 * (int64_t)h->A * C;
-  // |dE| <= B * max_d * 2C + 2A(2C + 1) must fit int32
-  const double bound = (double)B * maxd * 2.0 * C + 2.0 * h->A * (2.0 * C + 1.0);
+  // |dE| <= B * max_d * 2C + 2A(2C + 1) must fit int32 (B: the largest leg weight)
+  const double bound = (double)maxw * maxd * 2.0 * C + 2.0 * h->A * (2.0 * C + 1.0);
   if (bound >= 2147483647.0) return fail(QP_ERANGE, "|dE| bound %.3g exceeds int32", bound);
 
   h->Cp = round_up_i(C, 8);
@@ -343,11 +357,17 @@ extern "C" qp_status qp_build_qubo(const qp_field *f, int32_t A, int32_t B, int3
   }
   if (flags & QP_DENSE) {
     if (h->n > 65536) return fail(QP_ERANGE, "dense form of %lld variables is too large", (long long)h->n);
-    const int64_t maxS = std::max<int64_t>(2 * (int64_t)h->A, (int64_t)B * maxd);
+    const int64_t maxS = std::max<int64_t>(2 * (int64_t)h->A, maxw * maxd);
     h->S_i16 = maxS <= 32767;
     h->np = round_up_i((int)h->n, 8);
     QP_TRY(h->S_dev.ensure((size_t)h->n * h->np * (h->S_i16 ? 2 : 4)));
-    QP_CU(launch_build_dense(h->S_dev.p, h->S_i16, h->np, C, h->d32_dev.as<int32_t>(), h->A, B, 0));
+    DevBuf w_dev;
+    if (w) {
+      QP_TRY(w_dev.ensure((size_t)(C - 1) * 4));
+      QP_CU(cudaMemcpy(w_dev.p, w, (size_t)(C - 1) * 4, cudaMemcpyHostToDevice));
+    }
+    QP_CU(launch_build_dense(h->S_dev.p, h->S_i16, h->np, C, h->d32_dev.as<int32_t>(), h->A, B, 0,
+                             w ? w_dev.as<int32_t>() : nullptr));
     QP_CU(cudaDeviceSynchronize());
     std::vector<uint8_t> fr(h->n, 0), fv(h->n, 0);
     for (int t = 0; t < C; ++t)
@@ -361,6 +381,20 @@ extern "C" qp_status qp_build_qubo(const qp_field *f, int32_t A, int32_t B, int3
   }
   *out = h.release();
   return QP_OK;
+}
+
+extern "C" qp_status qp_build_qubo(const qp_field *f, int32_t A, int32_t B, int32_t scale, int32_t flags,
+                                   qp_handle **out) {
+  return build_field_qubo(f, A, B, scale, flags, nullptr, 0, out);
+}
+
+extern "C" qp_status qp_build_qubo_weighted(const qp_field *f, int32_t A, const int32_t *leg_weights,
+                                            int32_t n_legs, int32_t scale, qp_handle **out) {
+  if (!leg_weights) {
+    g_err.clear();
+    return fail(QP_EINVAL, "leg_weights must not be NULL");
+  }
+  return build_field_qubo(f, A, 1, scale, QP_STRUCTURED | QP_DENSE, leg_weights, n_legs, out);
 }
 
 extern "C" qp_status qp_build_from_dense(const int32_t *S, int64_t n, const uint8_t *frozen,
@@ -533,11 +567,13 @@ extern "C" qp_status qp_anneal_ex(qp_handle *h, int32_t R, const qp_schedule *sc
   if (o.replica_offset < 0 || (int64_t)o.replica_offset + R > INT32_MAX)
     return fail(QP_EINVAL, "replica_offset out of range");
   int kernel = o.kernel;
-  if (kernel == QP_KERNEL_AUTO) kernel = h->path ? QP_KERNEL_STRUCTURED : QP_KERNEL_DENSE;
+  if (kernel == QP_KERNEL_AUTO) kernel = h->path && !h->weighted ? QP_KERNEL_STRUCTURED : QP_KERNEL_DENSE;
   const bool structured = kernel == QP_KERNEL_STRUCTURED || kernel == QP_KERNEL_STRUCTURED_FLAT ||
                           kernel == QP_KERNEL_STRUCTURED_ROWS || kernel == QP_KERNEL_STRUCTURED_GROUP ||
                           kernel == QP_KERNEL_STRUCTURED_ROWS_SHARED;
   if (structured && !h->path) return fail(QP_EINVAL, "no structured form in this handle");
+  if (structured && h->weighted)
+    return fail(QP_EINVAL, "a handle with leg weights anneals with the dense kernel (the structured form is unweighted)");
   if (kernel == QP_KERNEL_DENSE && !h->has_dense) return fail(QP_EINVAL, "handle was built without QP_DENSE");
   if (!structured && kernel != QP_KERNEL_DENSE) return fail(QP_EINVAL, "unknown kernel %d", kernel);
   if (o.replicas_per_cta < 0 || o.replicas_per_cta > kMaxWarpsPerCta)
@@ -736,6 +772,7 @@ bool handle_struct_view(const qp_handle *h, StructView *out) {
   out->d_i16 = h->d_i16;
   out->max_d = h->max_d;
   out->d32 = h->d32_dev.as<int32_t>();
+  out->weighted = h->weighted;
   return true;
 }
 

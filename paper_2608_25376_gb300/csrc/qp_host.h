@@ -115,6 +115,7 @@ qp_status device_schedule(const qp_schedule &sc, DeviceSchedule *out, std::share
 struct qp_handle {
   int dev = 0;
   bool path = false;       // built from a field (structured terms available)
+  bool weighted = false;   // per-leg weights on the distance term: the dense form only
   int32_t C = 0, start = 0, A = 0, B = 0, max_d = 0;
   int64_t n = 0, c0 = 0;
   std::vector<int32_t> d;  // C x C (host)

@@ -124,8 +124,9 @@ cudaError_t launch_group(const StructArgs &a, bool d_i16, int warps_per_cta, cud
 cudaError_t launch_dense(const DenseArgs &a, bool s_i16, int warps_per_cta, cudaStream_t st,
                          LaunchInfo *info);
 bool dense_h_fits_smem(int64_t n, int C, int warps_per_cta);
+// w: per-leg weights (device, C-1 int32) in place of B, or null
 cudaError_t launch_build_dense(void *S, bool s_i16, int32_t np, int32_t C, const int32_t *d32,
-                               int32_t A, int32_t B, cudaStream_t st);
+                               int32_t A, int32_t B, cudaStream_t st, const int32_t *w = nullptr);
 cudaError_t launch_decode(const uint8_t *states, int32_t R, int32_t C, const int32_t *d32,
                           int32_t *paths, int64_t *lengths, cudaStream_t st);
 
@@ -159,6 +160,7 @@ struct StructView {
   const void *d;
   bool d_i16;
   const int32_t *d32;  // C x C int32 on the device
+  bool weighted;       // leg weights on the distance term (the structured kernels do not apply them)
 };
 bool handle_struct_view(const qp_handle *h, StructView *out);  // false for a generic QUBO
 // false if not cached on this device; *keep (may be NULL) holds the tables alive

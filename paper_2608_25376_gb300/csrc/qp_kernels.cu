@@ -620,9 +620,11 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_sweep_dense(const Dens
 }
 
 // ---------------------------------------------------------------------------
-// Dense form of Eq. 6 from the distance matrix (n x np, zero padding).
+// Dense form of Eq. 6 from the distance matrix (n x np, zero padding).  w:
+// one weight per leg (the leg from step t to t+1 gets w[t] in place of B; the
+// extended objective), or null.
 template <typename ST>
-__global__ void k_build_dense(ST *S, int np, int C, const int32_t *d, int A, int B) {
+__global__ void k_build_dense(ST *S, int np, int C, const int32_t *d, int A, int B, const int32_t *w) {
   const long long n = (long long)C * C;
   const long long total = n * np;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -636,7 +638,7 @@ __global__ void k_build_dense(ST *S, int np, int C, const int32_t *d, int A, int
       } else {
         if (u == t) v += 2 * A;
         if (j == i) v += 2 * A;
-        if (u == t + 1 || u + 1 == t) v += B * d[i * C + j];
+        if (u == t + 1 || u + 1 == t) v += (w ? w[min(t, u)] : B) * d[i * C + j];
       }
     }
     S[e] = (ST)v;
@@ -786,10 +788,10 @@ cudaError_t launch_dense(const DenseArgs &a, bool s_i16, int W, cudaStream_t st,
 }
 
 cudaError_t launch_build_dense(void *S, bool s_i16, int32_t np, int32_t C, const int32_t *d32,
-                               int32_t A, int32_t B, cudaStream_t st) {
+                               int32_t A, int32_t B, cudaStream_t st, const int32_t *w) {
   const int threads = 256, blocks = 152 * 8;
-  if (s_i16) k_build_dense<int16_t><<<blocks, threads, 0, st>>>(static_cast<int16_t *>(S), np, C, d32, A, B);
-  else k_build_dense<int32_t><<<blocks, threads, 0, st>>>(static_cast<int32_t *>(S), np, C, d32, A, B);
+  if (s_i16) k_build_dense<int16_t><<<blocks, threads, 0, st>>>(static_cast<int16_t *>(S), np, C, d32, A, B, w);
+  else k_build_dense<int32_t><<<blocks, threads, 0, st>>>(static_cast<int32_t *>(S), np, C, d32, A, B, w);
   return cudaGetLastError();
 }
 

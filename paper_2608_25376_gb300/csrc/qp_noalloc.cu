@@ -49,6 +49,7 @@ extern "C" qp_status qp_anneal_noalloc(qp_handle *h, int32_t R, const qp_schedul
   clear_error();
   StructView v;
   if (!h || !handle_struct_view(h, &v)) return set_error(QP_EINVAL, "qp_anneal_noalloc needs a handle built by qp_build_qubo");
+  if (v.weighted) return set_error(QP_EINVAL, "qp_anneal_noalloc: the structured form is unweighted: a handle with leg weights anneals with the dense kernel only");
   if (!sc || !states_out || !energies_out || R < 1 || replica_offset < 0 ||
       (int64_t)replica_offset + R > INT32_MAX)
     return set_error(QP_EINVAL, "qp_anneal_noalloc: bad argument");

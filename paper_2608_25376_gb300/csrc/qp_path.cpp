@@ -25,6 +25,7 @@ extern "C" qp_status qp_repair_batch(const qp_handle *hc, int32_t R, const uint8
   qp_handle *h = const_cast<qp_handle *>(hc);
   if (!h || !states || !paths_out || !lengths_out || R < 1) return fail(QP_EINVAL, "bad argument");
   if (!h->path) return fail(QP_EINVAL, "a generic QUBO has no path");
+  if (h->weighted) return fail(QP_EINVAL, "the repair's 2-opt shortens the unweighted length: not for a handle with leg weights");
   DevSet ds(h->dev);
   cudaStream_t st = static_cast<cudaStream_t>(stream_);
   const size_t n = (size_t)h->n;
@@ -91,6 +92,7 @@ extern "C" qp_status qp_anneal_timed(qp_handle *h, int32_t R, const qp_schedule 
   g_err.clear();
   if (!h || !sc || !path_out || !length_out || R < 1) return fail(QP_EINVAL, "bad argument");
   if (!h->path) return fail(QP_EINVAL, "qp_anneal_timed needs a handle built by qp_build_qubo");
+  if (h->weighted) return fail(QP_EINVAL, "qp_anneal_timed: the structured form is unweighted: a handle with leg weights anneals with the dense kernel only");
   if (!(time_limit_ms > 0.0) || !std::isfinite(time_limit_ms)) return fail(QP_EINVAL, "time_limit_ms must be > 0");
   qp_schedule full = *sc;
   full.sweep_begin = 0;

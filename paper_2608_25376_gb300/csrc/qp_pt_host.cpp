@@ -76,6 +76,7 @@ extern "C" qp_status qp_anneal_pt(qp_handle *h, int32_t G, const qp_pt_schedule 
   g_err.clear();
   if (!h || !pt || !states_out || !energies_out || G < 1) return fail(QP_EINVAL, "bad argument");
   if (!h->path) return fail(QP_EINVAL, "replica exchange needs a handle built by qp_build_qubo");
+  if (h->weighted) return fail(QP_EINVAL, "replica exchange: the structured form is unweighted: a handle with leg weights anneals with the dense kernel only");
   const int M = pt->levels, I = pt->sweeps_per_exchange, X = pt->exchanges;
   if (M < 2 || I < 1 || X < 1) return fail(QP_EINVAL, "need levels >= 2, sweeps_per_exchange >= 1, exchanges >= 1");
   if (!(pt->T_lo > 0.0) || !(pt->T_hi > pt->T_lo) || !std::isfinite(pt->T_hi))

@@ -27,7 +27,7 @@ QP_BATCH_D_SHARED = 2
 E_NONE = np.iinfo(np.int64).max
 
 # every entry point include/qpath.h declares
-SYMBOLS = ["qp_build_qubo", "qp_build_from_dense", "qp_qubo_info", "qp_export_dense", "qp_export_dist",
+SYMBOLS = ["qp_build_qubo", "qp_build_qubo_weighted", "qp_build_from_dense", "qp_qubo_info", "qp_export_dense", "qp_export_dist",
            "qp_thresholds", "qp_anneal", "qp_anneal_ex", "qp_anneal_noalloc", "qp_batch_create",
            "qp_batch_run", "qp_batch_info", "qp_batch_destroy", "qp_anneal_batch", "qp_decode_path",
            "qp_decode_batch", "qp_repair_batch", "qp_repair_path", "qp_anneal_timed", "qp_anneal_pt", "qp_ws_create", "qp_ws_destroy", "qp_ws_param_count", "qp_ws_get_params",
@@ -94,6 +94,7 @@ def lib():
             P = ct.POINTER
             sig = {
                 "qp_build_qubo": [P(qp_field), i32, i32, i32, i32, P(vp)],
+                "qp_build_qubo_weighted": [P(qp_field), i32, vp, i32, i32, P(vp)],
                 "qp_build_from_dense": [vp, i64, vp, vp, i64, P(vp)],
                 "qp_qubo_info": [vp, P(i64), P(i32), P(i64), P(i32), P(i32)],
                 "qp_export_dense": [vp, vp],
@@ -216,6 +217,18 @@ def qp_build_qubo(field, A=0, B=1, scale=100, flags=QP_STRUCTURED) -> Handle:
     f = qp_field(int(field.rows), int(field.cols), None if mask is None else mask.ctypes.data, int(field.start))
     out = ct.c_void_p()
     _check(lib().qp_build_qubo(ct.byref(f), int(A), int(B), int(scale), int(flags), ct.byref(out)))
+    return Handle(out)
+
+
+def qp_build_qubo_weighted(field, leg_weights, A=0, scale=100) -> Handle:
+    """The path QUBO with one weight per leg on the distance term (C - 1
+    non-negative integers; see objectives.payload_leg_weights); the handle
+    anneals with the dense kernel."""
+    mask = None if field.free_mask is None else np.ascontiguousarray(field.free_mask, np.uint8)
+    f = qp_field(int(field.rows), int(field.cols), None if mask is None else mask.ctypes.data, int(field.start))
+    w = np.ascontiguousarray(leg_weights, np.int32)
+    out = ct.c_void_p()
+    _check(lib().qp_build_qubo_weighted(ct.byref(f), int(A), _ptr(w), int(w.size), int(scale), ct.byref(out)))
     return Handle(out)
 
 
