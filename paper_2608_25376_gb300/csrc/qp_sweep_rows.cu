@@ -101,24 +101,18 @@ __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_
     if (C > 2) row_field<DT, NCH, DMODE>(st, Cw, hot1, 2, d, Cp, C, lane, N1);
     if (LA == 2 && C > 3) row_field<DT, NCH, DMODE>(st, Cw, hot1, 3, d, Cp, C, lane, N2);
     int hl = C > 2 + LA ? hot1[2 + LA] : -1;  // the single cell of row t+1+LA
-    int xnn[NCH];
-#pragma unroll
-    for (int c = 0; c < NCH; ++c)
-      xnn[c] = 128 * c + 4 * lane < C ? (int)((st[Cw + 4 * c + (lane >> 3)] >> (4 * (lane & 7))) & 0xFu) : 0;
+    int hc = hot1[1];                          // the single cell of row t
     for (int t = 1; t < C; ++t) {
       uint32_t *row = st + t * Cw;
       int xn[NCH];
-      int rt = 0;
+      int rt;
 #pragma unroll
-      for (int c = 0; c < NCH; ++c) {
-        xn[c] = xnn[c];
-        rt += __popc(xn[c]);
+      for (int c = 0; c < NCH; ++c)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           N[c][j] = N1[c][j];
           if (LA == 2) N1[c][j] = N2[c][j];
         }
-      }
       // F_{t+1+LA}: the d row of that row's single hot cell, else a scan of its bits
       if (t + 1 + LA < C && hl >= 0) {
         set_drow<DT, NCH, DMODE>(d, Cp, C, hl, lane, NL);
@@ -130,11 +124,21 @@ __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_
         }
       }
       hl = t + 2 + LA < C ? hot1[t + 2 + LA] : -1;
+      const int hcn = t + 1 < C ? hot1[t + 1] : -1;
+      // row t's sum: 1 from the cache when the row holds exactly one cell (its
+      // bit groups are then derived only if the row needs the exact evaluation),
+      // else from its bits
+      if (hc >= 0) {
+        rt = 1;
+      } else {
+        rt = 0;
 #pragma unroll
-      for (int c = 0; c < NCH; ++c)
-        xnn[c] = (t + 1 < C && 128 * c + 4 * lane < C)
-                     ? (int)((row[Cw + 4 * c + (lane >> 3)] >> (4 * (lane & 7))) & 0xFu) : 0;
-      rt = __reduce_add_sync(kFull, rt);
+        for (int c = 0; c < NCH; ++c) {
+          xn[c] = 128 * c + 4 * lane < C ? (int)((row[4 * c + (lane >> 3)] >> (4 * (lane & 7))) & 0xFu) : 0;
+          rt += __popc(xn[c]);
+        }
+        rt = __reduce_add_sync(kFull, rt);
+      }
       const int rt0 = rt;
       bool flipped = false;
       const int tC = t * C;
@@ -159,6 +163,10 @@ __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_
         }
       }
       if (__any_sync(kFull, maybe)) {
+        if (hc >= 0) {
+#pragma unroll
+          for (int c = 0; c < NCH; ++c) xn[c] = (hc >> 2) == 32 * c + lane ? 1 << (hc & 3) : 0;
+        }
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
           if (128 * c >= C) break;
@@ -196,6 +204,7 @@ __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_
           P[c][j] = Cu[c][j];
           Cu[c][j] = N[c][j];
         }
+      hc = hcn;
     }
     if (viol == 0 && E < best) best = E;
     settled = a.skip_settled && !any_hit;
