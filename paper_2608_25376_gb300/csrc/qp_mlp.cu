@@ -301,6 +301,8 @@ __global__ void __launch_bounds__(128)
           atomicAdd(o + 1, x.y);
           atomicAdd(o + 2, x.z);
           atomicAdd(o + 3, x.w);
+        } else if (g.mode == kEpiPartialF32) {
+          *reinterpret_cast<float4 *>(g.out_f32 + (size_t)blockIdx.z * g.M * g.ldo + (size_t)row * g.ldo + col) = x;
         } else {
           float a = x.x, b = x.y, c = x.z, e = x.w;
           if (g.mode == kEpiReluMask) {  // gradient through the ReLU of the stored activation
@@ -570,9 +572,10 @@ __global__ void __launch_bounds__(kFwdThreads)
 
 // Softmax cross-entropy over the valid steps t < steps[m] of each cell row;
 // rows with label < 0 are padding.  dZ = (softmax - onehot) * inv_rows (bf16),
-// loss_sum += -log p[label].  One warp per row, 8 columns per lane.
+// loss_rows[m] = -log p[label] (0 for padding).  One warp per row, 8 columns
+// per lane.
 __global__ void k_softmax_ce(const float *Z, int ldz, const int32_t *label, const int32_t *steps, int M,
-                             float inv_rows, __nv_bfloat16 *dZ, int ldd, float *loss_sum) {
+                             float inv_rows, __nv_bfloat16 *dZ, int ldd, float *loss_rows) {
   const int lane = threadIdx.x & 31;
   const int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (m >= M) return;
@@ -606,21 +609,47 @@ __global__ void k_softmax_ce(const float *Z, int ldz, const int32_t *label, cons
     }
     *reinterpret_cast<__nv_bfloat162 *>(d + t) = __floats2bfloat162_rn(g0, g1);
   }
-  if (y >= 0 && lane == (y >> 3)) {
+  if (y < 0) {
+    if (lane == 0) loss_rows[m] = 0.0f;
+  } else if (lane == (y >> 3)) {
     const float py = v[y & 7] / s;
-    atomicAdd(loss_sum, -logf(fmaxf(py, 1e-30f)));
+    loss_rows[m] = -logf(fmaxf(py, 1e-30f));
   }
 }
 
-// db[n] += sum_m dY[m][n] over a slab of rows (fp32 atomics).
-__global__ void k_colsum(const __nv_bfloat16 *Y, int ld, int M, int N, float *out) {
+// partial[slab][n] = sum of Y[m][n] over the slab's rows, in row order.
+__global__ void k_colsum(const __nv_bfloat16 *Y, int ld, int M, int N, float *partial) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const int rows_per = (M + gridDim.y - 1) / gridDim.y;
   const int r0 = blockIdx.y * rows_per, r1 = min(M, r0 + rows_per);
   float s = 0.0f;
   for (int m = r0; m < r1; ++m) s += __bfloat162float(Y[(size_t)m * ld + n]);
-  atomicAdd(out + n, s);
+  partial[(size_t)blockIdx.y * N + n] = s;
+}
+
+// out[i] = sum_{z < Z} ws[z * n + i], z in increasing order.
+__global__ void k_sum_splits(const float *ws, int Z, int n, float *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = 0.0f;
+  for (int z = 0; z < Z; ++z) s += ws[(size_t)z * n + i];
+  out[i] = s;
+}
+
+// out[0] = sum of v[0 .. n-1] in a fixed order: thread j sums j, j+256, ...;
+// then thread 0 adds the 256 partial sums in order.
+__global__ void __launch_bounds__(256) k_sum_ordered(const float *v, int n, float *out) {
+  __shared__ float part[256];
+  float s = 0.0f;
+  for (int i = threadIdx.x; i < n; i += 256) s += v[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int j = 0; j < 256; ++j) t += part[j];
+    out[0] = t;
+  }
 }
 
 // out[c][r] = in[r][c] for a bf16 R x C matrix (32 x 32 tiles).
@@ -703,6 +732,17 @@ bool tile_map(CUtensorMap *map, const __nv_bfloat16 *base, int rows, int K, int 
 
 }  // namespace
 
+int gemm_splits(int K, int splits) {
+  int kps = (K + splits - 1) / splits;
+  kps = (kps + kChunkK - 1) / kChunkK * kChunkK;
+  return (K + kps - 1) / kps;
+}
+
+cudaError_t sum_splits(const float *ws, int splits, int n, float *out, cudaStream_t st) {
+  k_sum_splits<<<(n + 255) / 256, 256, 0, st>>>(ws, splits, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t gemm(const GemmArgs &g, int splits, cudaStream_t st) {
   if (g.N < 16 || g.N > 256 || (g.N & 15) || (g.K & 15) || (g.lda & 7) || (g.ldb & 7) || (g.ldo & 3) ||
       (g.mode == kEpiReluMask && (g.ldr & 3)) || splits < 1)
@@ -739,15 +779,16 @@ cudaError_t forward(const FwdArgs &g, const __nv_bfloat16 *const w[4], cudaStrea
 }
 
 cudaError_t softmax_ce(const float *Z, int ldz, const int32_t *label, const int32_t *steps, int M, float inv_rows,
-                       __nv_bfloat16 *dZ, int ldd, float *loss_sum, cudaStream_t st) {
-  k_softmax_ce<<<(M + 7) / 8, 256, 0, st>>>(Z, ldz, label, steps, M, inv_rows, dZ, ldd, loss_sum);
+                       __nv_bfloat16 *dZ, int ldd, float *loss_rows, float *loss_sum, cudaStream_t st) {
+  k_softmax_ce<<<(M + 7) / 8, 256, 0, st>>>(Z, ldz, label, steps, M, inv_rows, dZ, ldd, loss_rows);
+  k_sum_ordered<<<1, 256, 0, st>>>(loss_rows, M, loss_sum);
   return cudaGetLastError();
 }
 
-cudaError_t colsum(const __nv_bfloat16 *Y, int ld, int M, int N, float *out, cudaStream_t st) {
-  dim3 grid((N + 127) / 128, 64);
-  k_colsum<<<grid, 128, 0, st>>>(Y, ld, M, N, out);
-  return cudaGetLastError();
+cudaError_t colsum(const __nv_bfloat16 *Y, int ld, int M, int N, float *partial, float *out, cudaStream_t st) {
+  dim3 grid((N + 127) / 128, kColsumSlabs);
+  k_colsum<<<grid, 128, 0, st>>>(Y, ld, M, N, partial);
+  return sum_splits(partial, kColsumSlabs, N, out, st);
 }
 
 cudaError_t transpose(const __nv_bfloat16 *in, int R, int Cc, int ldi, __nv_bfloat16 *out, int ldo,

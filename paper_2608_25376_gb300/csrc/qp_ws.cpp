@@ -84,6 +84,7 @@ struct qp_ws {
   int cap = 0;                         // rows the activation buffers hold
   int fwd_mode = QP_WS_FORWARD_FUSED;
   Buf x0, h[3], z, dz, dh[3], t1, t2, lab, stp, loss, err;
+  Buf gws, cws, lrow;  // split-K partials, column-sum partials, per-row losses (fixed-order sums)
 };
 
 namespace {
@@ -108,6 +109,8 @@ qp_status ensure_rows(qp_ws *m, int Mp) {
   WS_ALLOC(m->t2, (size_t)Mp * kHid * 2);
   WS_ALLOC(m->lab, (size_t)Mp * 4);
   WS_ALLOC(m->stp, (size_t)Mp * 4);
+  WS_ALLOC(m->lrow, (size_t)Mp * 4);
+  WS_ALLOC(m->cws, (size_t)mlp::kColsumSlabs * kOut * 4);
   m->cap = Mp;
   return QP_OK;
 }
@@ -198,12 +201,14 @@ qp_status forward(qp_ws *m, int Mp, bool keep_hidden, cudaStream_t st) {
 }
 
 // Gradients of the mean cross-entropy into gw/gb (fp32); loss sum into m->loss.
+// Every sum over rows is taken in a fixed order (split-K partials and slabs
+// added in index order, no atomics), so a training run repeats bit for bit.
 qp_status backward(qp_ws *m, int M, int Mp, cudaStream_t st) {
-  WS_CU(cudaMemsetAsync(m->loss.p, 0, 4, st));
   WS_CU(mlp::softmax_ce(m->z.as<float>(), kOut, m->lab.as<int32_t>(), m->stp.as<int32_t>(), Mp, 1.0f / (float)M,
-                        m->dz.as<__nv_bfloat16>(), kOut, m->loss.as<float>(), st));
+                        m->dz.as<__nv_bfloat16>(), kOut, m->lrow.as<float>(), m->loss.as<float>(), st));
   const __nv_bfloat16 *dy = m->dz.as<__nv_bfloat16>();
   const int splits = std::max(1, Mp / 512);
+  WS_ALLOC(m->gws, (size_t)mlp::gemm_splits(Mp, splits) * kHid * kHid * 4);
   for (int l = kLayers - 1; l >= 0; --l) {
     const int nout = kDimOut[l], nin = kDimIn[l];
     const __nv_bfloat16 *x = l == 0 ? m->x0.as<__nv_bfloat16>() : m->h[l - 1].as<__nv_bfloat16>();
@@ -211,13 +216,12 @@ qp_status backward(qp_ws *m, int M, int Mp, cudaStream_t st) {
     __nv_bfloat16 *dyt = m->t1.as<__nv_bfloat16>(), *xt = m->t2.as<__nv_bfloat16>();
     WS_CU(mlp::transpose(dy, Mp, nout, nout, dyt, Mp, st));
     WS_CU(mlp::transpose(x, Mp, nin, nin, xt, Mp, st));
-    WS_CU(cudaMemsetAsync(m->gw[l].p, 0, (size_t)nout * nin * 4, st));
-    WS_CU(cudaMemsetAsync(m->gb[l].p, 0, (size_t)nout * 4, st));
-    mlp::GemmArgs g = gargs(dyt, Mp, xt, Mp, nout, nin, Mp, mlp::kEpiAtomicF32, m->err.as<int>());
-    g.out_f32 = m->gw[l].as<float>();
+    mlp::GemmArgs g = gargs(dyt, Mp, xt, Mp, nout, nin, Mp, mlp::kEpiPartialF32, m->err.as<int>());
+    g.out_f32 = m->gws.as<float>();
     g.ldo = nin;
     WS_CU(mlp::gemm(g, splits, st));
-    WS_CU(mlp::colsum(dy, nout, Mp, nout, m->gb[l].as<float>(), st));
+    WS_CU(mlp::sum_splits(m->gws.as<float>(), mlp::gemm_splits(Mp, splits), nout * nin, m->gw[l].as<float>(), st));
+    WS_CU(mlp::colsum(dy, nout, Mp, nout, m->cws.as<float>(), m->gb[l].as<float>(), st));
     if (l == 0) break;
     // dX[m][in] = relu'(X) * sum_out dY[m][out] W[out][in]  (B = W^T, out contiguous)
     mlp::GemmArgs gx = gargs(dy, nout, m->wt[l].as<__nv_bfloat16>(), nout, Mp, nin, nout, mlp::kEpiReluMask,

@@ -133,3 +133,18 @@ def test_fused_forward_equals_layered(dev):
     qpath.qp_ws_set_forward_mode(m, qpath.QP_WS_FORWARD_FUSED)
     with pytest.raises(qpath.QpError):
         qpath.qp_ws_set_forward_mode(m, 2)
+
+
+def test_training_repeats_bit_for_bit(dev):
+    """Every sum over rows in a training step is taken in a fixed order, so two
+    models from the same seed trained on the same batches end with the same
+    weights, moments and losses, bit for bit (split-K included: 8960 rows)."""
+    X, Y, T = field_batch(140, seed=9)
+    X, Y, T = X[:8960], Y[:8960], T[:8960]
+    runs = []
+    for _ in range(2):
+        m = qpath.WarmStartModel(seed=21)
+        losses = [qpath.qp_ws_train_step(m, X, Y, T, 1e-3) for _ in range(3)]
+        runs.append((losses, qpath.qp_ws_get_params(m)))
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1].view(np.uint32), runs[1][1].view(np.uint32))
