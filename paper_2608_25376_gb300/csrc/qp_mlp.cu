@@ -295,12 +295,6 @@ __global__ void __launch_bounds__(128)
         const size_t col = (size_t)(c0 + cl);
         if (g.mode == kEpiBiasF32) {
           *reinterpret_cast<float4 *>(g.out_f32 + (size_t)row * g.ldo + col) = x;
-        } else if (g.mode == kEpiAtomicF32) {
-          float *o = g.out_f32 + (size_t)row * g.ldo + col;
-          atomicAdd(o, x.x);
-          atomicAdd(o + 1, x.y);
-          atomicAdd(o + 2, x.z);
-          atomicAdd(o + 3, x.w);
         } else if (g.mode == kEpiPartialF32) {
           *reinterpret_cast<float4 *>(g.out_f32 + (size_t)blockIdx.z * g.M * g.ldo + (size_t)row * g.ldo + col) = x;
         } else {

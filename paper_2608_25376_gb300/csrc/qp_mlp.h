@@ -11,7 +11,6 @@ namespace mlp {
 enum EpiMode {
   kEpiBiasRelu = 0,   // out_bf16 = bf16(relu(acc + bias))
   kEpiBiasF32 = 1,    // out_f32 = acc + bias
-  kEpiAtomicF32 = 2,  // out_f32 += acc (split-K, in no fixed order)
   kEpiPartialF32 = 4, // out_f32 + z * M * ldo = acc for split z (sum_splits adds them in order)
   kEpiReluMask = 3,   // out_bf16 = bf16(relu_ref > 0 ? acc : 0)
 };
