@@ -61,6 +61,30 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+// The same generator with its key given as the seed's two words (round keys
+// computed on the fly) or as the ten rounds' keys k0 + i W0, k1 + i W1
+// computed once (launch constants, read straight from the kernel's argument
+// block by the XORs).
+struct PhiloxKey {
+  uint32_t k0, k1;
+};
+struct RoundKeys {
+  uint32_t k[20];  // k[2i] = k0 + i 0x9E3779B9, k[2i+1] = k1 + i 0xBB67AE85
+};
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKey &key) {
+  return philox4x32_10(c, key.k0, key.k1);
+}
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys &rk) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+    const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+    const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
+    c = make_uint4(hi1 ^ c.y ^ rk.k[2 * i], lo1, hi0 ^ c.w ^ rk.k[2 * i + 1], lo0);
+  }
+  return c;
+}
+
 __device__ __forceinline__ uint32_t word_of(const uint4 &u, int j) {
   return j == 0 ? u.x : (j == 1 ? u.y : (j == 2 ? u.z : u.w));
 }

@@ -189,13 +189,13 @@ __device__ __forceinline__ bool row_pretest_shifted(const int (&P)[NCH][4], cons
 // first accepted one, apply it, resume after it.  Returns whether any flip was
 // applied.  SG: the row's bits are in global memory (flipped by a fire-and-
 // forget atomic XOR, so the warp never waits on the write).
-template <typename DT, int NCH, int DMODE, bool SG = false>
+template <typename DT, int NCH, int DMODE, bool SG = false, typename KEY = PhiloxKey>
 __device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int (&base)[4], const int (&de0)[4],
                                        int &xnc, int validc,
                                        int (&tAc)[4], int &rt, int (&Cu)[NCH][4], uint32_t *row, long long &E,
                                        long long &acc, int &viol, const void *d, int Cp, int C, int lane, int twoA,
                                        int len, unsigned lenm1, float cT, int dq, uint32_t Q, const uint32_t *thr,
-                                       uint32_t rg, uint32_t key0, uint32_t key1, int tshift = 0) {
+                                       uint32_t rg, const KEY &key, int tshift = 0) {
   const int ib = 128 * c + 4 * lane;
   const int delta = tC & 3;
   int cand = validc;
@@ -220,7 +220,7 @@ __device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int
       const int m0 = (1 << (4 - delta)) - 1;
       const uint32_t b0 = (uint32_t)((tC + ib) >> 2);
       if (!h0) {
-        u0 = philox4x32_10(make_uint4(b0, (uint32_t)s, rg, kRngTag), key0, key1);
+        u0 = philox4x32_10(make_uint4(b0, (uint32_t)s, rg, kRngTag), key);
         u1.x = __shfl_down_sync(kFull, u0.x, 1);
         u1.y = __shfl_down_sync(kFull, u0.y, 1);
         u1.z = __shfl_down_sync(kFull, u0.z, 1);
@@ -228,7 +228,7 @@ __device__ __forceinline__ bool row_chunk(int c, int t, int s, int tC, const int
         h0 = true;
       }
       if (lane == 31 && (need & ~m0) && !h1) {
-        u1 = philox4x32_10(make_uint4(b0 + 1, (uint32_t)s, rg, kRngTag), key0, key1);
+        u1 = philox4x32_10(make_uint4(b0 + 1, (uint32_t)s, rg, kRngTag), key);
         h1 = true;
       }
       // the lane's four draws: words delta..delta+3 of the blocks (u0, u1); delta

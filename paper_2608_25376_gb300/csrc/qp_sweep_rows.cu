@@ -187,7 +187,7 @@ __device__ __forceinline__ void rows_replica(const StructArgs &a, int r, uint32_
             any_hit = true;
             flipped |= row_chunk<DT, NCH, DMODE>(c, t, s, tC, base, de, xn[c], validc[c], tAc[c], rt, Cu, row, E,
                                                  acc, viol, d, Cp, C, lane, twoA, len, lenm1, cT, dq, Q, thr, rg,
-                                                 a.key0, a.key1);
+                                                 PhiloxKey{a.key0, a.key1});
           }
         }
       }
@@ -365,7 +365,8 @@ __device__ __forceinline__ bool rows_g_flip(const StructArgs &a, uint32_t *st, i
                                             const int (&P)[NCH][4], int (&Cu)[NCH][4], const int (&N)[NCH][4],
                                             int (&tAc)[NCH][4], const int (&validc)[NCH], long long &E,
                                             long long &acc, int &viol, int twoA, int len, unsigned lenm1, float cT,
-                                            int dq, uint32_t Q, const uint32_t *thr, uint32_t rg) {
+                                            int dq, uint32_t Q, const uint32_t *thr, uint32_t rg,
+                                            const RoundKeys &rk) {
   uint32_t *row = st + (size_t)t * Cw;
   const int rt0 = rt;
   const int B = a.B;
@@ -395,8 +396,7 @@ __device__ __forceinline__ bool rows_g_flip(const StructArgs &a, uint32_t *st, i
     if (__any_sync(kFull, hit & validc[c])) {
       any_hit = true;
       flipped |= row_chunk<DT, NCH, 0, true>(c, t, s, tC, base, de, xn[c], validc[c], tAc[c], rt, Cu, row, E, acc,
-                                             viol, d, Cp, C, lane, twoA, len, lenm1, cT, dq, Q, thr, rg, a.key0,
-                                             a.key1, len);
+                                             viol, d, Cp, C, lane, twoA, len, lenm1, cT, dq, Q, thr, rg, rk, len);
     }
   }
   viol += (rt != 1) - (rt0 != 1);
@@ -424,7 +424,7 @@ __device__ __forceinline__ bool rows_g_flip(const StructArgs &a, uint32_t *st, i
 template <typename DT, int NCH, int K>
 __device__ __forceinline__ void rows_replica_g(const StructArgs &a, int r, uint32_t *st, int16_t *hot, DT *ring,
                                                int lane, int sb, int se, bool fresh, bool last, long long &best,
-                                               long long &acc) {
+                                               long long &acc, const RoundKeys &rk) {
   static_assert(K >= 3, "the ring holds rows t+2 .. t+K+1");
   const int C = a.C, Cp = a.Cp, s0 = a.start, A = a.A, B = a.B;
   const int twoA = 2 * A;
@@ -517,7 +517,7 @@ __device__ __forceinline__ void rows_replica_g(const StructArgs &a, int r, uint3
       if (rows_g_front<DT, NCH, K>(st, hot, ring, d, Cp, C, Cw, lane, t, hn, X0, X2, X3, tAc, rtst, rt, xn)) {
       flip:
         any_hit |= rows_g_flip<DT, NCH>(a, st, hot, d, Cp, C, Cw, lane, t, s, hn, rt, xn, X0, X1, X2, tAc, validc,
-                                        E, acc, viol, twoA, len, lenm1, cT, dq, Q, thr, rg);
+                                        E, acc, viol, twoA, len, lenm1, cT, dq, Q, thr, rg, rk);
       }
 #pragma unroll
       for (int c = 0; c < NCH; ++c)
@@ -567,7 +567,8 @@ constexpr long long kSegmentWaitCycles = 20000000000LL;  // ~10 s at 2 GHz (a un
 
 template <typename DT, int NCH>
 __global__ void __launch_bounds__(kRowsGMaxWarps * 32)
-    k_sweep_rows_g(const StructArgs a, int G, int *counter, int *progress, long long *carry, int *err) {
+    k_sweep_rows_g(const StructArgs a, const RoundKeys rk, int G, int *counter, int *progress, long long *carry,
+                   int *err) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const size_t hot_bytes = align16r(2 * (size_t)a.C);
@@ -612,7 +613,7 @@ __global__ void __launch_bounds__(kRowsGMaxWarps * 32)
     }
     const bool last = g == G - 1;
     rows_replica_g<DT, NCH, kRowsGRing>(a, r, a.gstate + (size_t)r * a.nw_pad, hot, ring, lane, sb, se, g == 0, last,
-                                        best, acc);
+                                        best, acc, rk);
     __syncwarp();
     if (!last && lane == 0) {
       carry[2 * (size_t)r] = best;
@@ -976,15 +977,21 @@ cudaError_t launch_rows_g(const StructArgs &a_in, bool d_i16, int W, int *counte
     info->smem = smem;
     info->variant = G > 1 ? "rows,spins:global,d:L2 ring,segments" : "rows,spins:global,d:L2 ring";
   }
+  // the ten rounds' Philox keys, launch constants
+  RoundKeys rk;
+  for (int i = 0; i < 10; ++i) {
+    rk.k[2 * i] = a.key0 + (uint32_t)i * 0x9E3779B9u;
+    rk.k[2 * i + 1] = a.key1 + (uint32_t)i * 0xBB67AE85u;
+  }
   std::lock_guard<std::mutex> lk(launch_mutex());
   if (d_i16) {
     auto k = k_sweep_rows_g<int16_t, 4>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) k<<<blocks, W * 32, smem, st>>>(a, G, counter, progress, carry, err);
+    if (e == cudaSuccess) k<<<blocks, W * 32, smem, st>>>(a, rk, G, counter, progress, carry, err);
   } else {
     auto k = k_sweep_rows_g<int32_t, 4>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) k<<<blocks, W * 32, smem, st>>>(a, G, counter, progress, carry, err);
+    if (e == cudaSuccess) k<<<blocks, W * 32, smem, st>>>(a, rk, G, counter, progress, carry, err);
   }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
