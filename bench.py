@@ -9,7 +9,7 @@ the QUBO from the host field and reads every result back to pinned host memory
 inside the timed region, through the same C ABI a user calls.
 
 Workload (default, the largest single-GPU configuration): 24x24 field, 15%
-obstacles dropped by a seeded Bernoulli draw (490 cells, n = 240,100
+obstacles dropped by a seeded Bernoulli draw (491 cells, n = 241,081
 variables), int16 distances, structured terms only, int32 dE / int64
 energies, 4096 replicas x 10000 sweeps, geometric T 1e3 -> 1, seed 1.
 flip attempts = R * S * (C-1)^2.  The 10x10 workload (92 cells, 1024 x 5000,
