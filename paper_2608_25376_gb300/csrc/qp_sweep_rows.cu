@@ -477,10 +477,12 @@ __device__ __forceinline__ void rows_replica_g(const StructArgs &a, int r, uint3
     int hn = hot[1];
     const RowTest rtst{B, twoA, len, C, (unsigned)(2 * twoA - 2 * len)};
     int rt, xn[NCH];
-    if (len <= A) {
-      // A cold sweep: a row whose cells form a permutation with the rest of
-      // the state has every dE >= A >= len, so almost every row is cleared
-      // by the whole-row test and changes nothing.  Four of them run with
+    if (len <= twoA) {
+      // A cold sweep: in a row whose cells form a permutation with the rest of
+      // the state, adding a cell costs dE >= 2A >= len and removing its own
+      // costs dE = 2A - P - N >= A, inside the band only when len comes within
+      // P + N of 2A, so almost every row is cleared by the whole-row test and
+      // changes nothing.  Four of them run with
       // the fields' roles rotated, (P, N, F_{t+2}) = (X0, X2, X3), (X1, X3,
       // X0), (X2, X0, X1), (X3, X1, X2), so no register moves; this loop
       // holds no flip path (which keeps its registers free), and the first
